@@ -1,0 +1,27 @@
+"""Oracle for the fixed-sector fermionic state-vector path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+baseline leg of the benchmark may import anything from this package.  The
+product path (the CUDA library and its Python binding) never calls it, and
+shares no code, tables or constants with it.
+
+Plain, slow, obviously-correct complex128 NumPy/SciPy code written from the
+paper: string addresses (§3.1), number-operator-sum and diagonal-Coulomb
+evolution (§3.2.1, §3.2.2), orbital rotations by minor determinants (§2.3)
+and by Givens rotations (§3.2.3), the LUCJ ansatz (§4.3, §4.5.1) and its
+gradient.  Each function is pinned by tests that do not reuse it: a dense
+Jordan-Wigner construction with matrix exponentials (`bruteforce`), the
+Slater-determinant closed form (§2.4), the group-homomorphism identities of
+§2.3, the gate equivalences listed after Table 1, the state sizes printed in
+§1, §5.2 and §6.1, and finite differences for the gradient.
+"""
+
+from .strings import strings, address_map, occupations, excite
+from .gates import (dims, hartree_fock, apply_num_op_sum_evolution,
+                    apply_diag_coulomb_evolution, diag_coulomb_angle,
+                    minor_matrix, apply_orbital_rotation,
+                    apply_orbital_rotation_minors, apply_orbital_rotation_givens,
+                    apply_givens, givens_matrix, givens_decomposition,
+                    slater_from_hf)
+from .lucj import (lucj_forward, lucj_vjp, transition_one_body,
+                   expm_frechet_adjoint)
