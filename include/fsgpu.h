@@ -1,0 +1,163 @@
+/*
+ * fsgpu: fixed-sector fermionic state vectors on one GB300 GPU (sm_103a).
+ *
+ * C ABI of libfsgpu.so.  No C++ or PyTorch types cross this boundary:
+ * pointers are plain device or host addresses, sizes are plain integers and
+ * a stream is passed as `void *` holding a cudaStream_t (NULL = the legacy
+ * default stream).
+ *
+ * State layout (the paper's state-vector representation, §3.1): a state in
+ * the sector (norb, n_alpha, n_beta) is a row-major dim_a x dim_b complex
+ * matrix, dim_s = C(norb, n_s).  Element (i, j) is the coefficient of the
+ * configuration |I_a, I_b> = cre_b(I_b) cre_a(I_a)|vac> (§2.2, §2.5) whose
+ * alpha string has address i and beta string address j.  The address of a
+ * string (occupied-orbital bitmask, bit p = orbital p) is its position among
+ * all strings with the same electron count listed in ascending integer
+ * order; equivalently sum_k C(o_k, k+1) over the occupied orbitals
+ * o_0 < o_1 < ... (combinatorial number system).  The Hartree-Fock string
+ * {0, ..., n-1} has address 0.  Complex numbers are interleaved (re, im):
+ * FS_C64 = two floats, FS_C128 = two doubles.  A state pointer must be
+ * 16-byte aligned.
+ *
+ * Ownership: every state/cotangent pointer belongs to the caller, who
+ * allocates and frees it; the library updates it in place and never keeps
+ * it after the call returns.  The library owns its context, its cached
+ * string tables and its scratch buffers (allocated on first use for a
+ * sector, freed by fs_destroy).
+ *
+ * Host matrices are row-major `const double *`; an N x N complex matrix is
+ * 2*N*N doubles (interleaved re, im); a real N x N matrix is N*N doubles.
+ *
+ * Asynchrony: calls enqueue work on `stream` and return; host inputs are
+ * copied before the call returns, so they may be reused at once.  Calls
+ * that return host outputs (fs_lucj_vjp gradients, fs_string_table,
+ * fs_excitation_table) synchronize the stream before returning.
+ *
+ * Errors: every call returns an fs_status.  Argument errors are detected on
+ * the host before any work is enqueued and leave the state untouched.
+ * fs_last_error() returns a per-thread message for the last failure.
+ * Kernels that can fail on the device (bounded waits, index checks) record
+ * a code in the context's device status word; fs_sync_status() reads and
+ * clears it.
+ */
+#ifndef FSGPU_H
+#define FSGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FS_OK = 0,
+  FS_ERR_ARG = -1,         /* invalid argument (sizes, pointers, alignment) */
+  FS_ERR_NOT_UNITARY = -2, /* a matrix that must be unitary is not (1e-10) */
+  FS_ERR_NOMEM = -3,       /* device or host allocation failed */
+  FS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  FS_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  FS_ERR_BOUNDS = -6,      /* a device-side index check failed */
+  FS_ERR_UNSUPPORTED = -7  /* valid request outside what this build supports */
+} fs_status;
+
+typedef enum { FS_C64 = 0, FS_C128 = 1 } fs_dtype;
+
+/* Orbital-rotation method: Givens sweeps (§3.2.3), dense minor-matrix
+ * products (§2.3), or the faster of the two as measured by the library's
+ * autotuner for the sector and dtype. */
+typedef enum { FS_ROT_AUTO = 0, FS_ROT_GIVENS = 1, FS_ROT_MINORS = 2 } fs_rot_path;
+
+typedef struct fs_ctx fs_ctx;
+
+/* Create a context bound to CUDA device `device`.  The device must be an
+ * sm_103 GPU.  Returns FS_ERR_ARG for a bad device index. */
+int fs_create(fs_ctx **ctx, int device);
+/* Free the context, its tables and scratch.  Synchronizes the device. */
+int fs_destroy(fs_ctx *ctx);
+/* Message of the last failing call on this host thread ("" if none). */
+const char *fs_last_error(void);
+/* Wait for `stream`, then read and clear the device status word.  Returns
+ * FS_OK, FS_ERR_TIMEOUT or FS_ERR_BOUNDS, or FS_ERR_CUDA if the stream
+ * itself failed. */
+int fs_sync_status(fs_ctx *ctx, void *stream);
+
+/* Force or release the orbital-rotation method (default FS_ROT_AUTO). */
+int fs_set_rotation_path(fs_ctx *ctx, int path);
+
+/* Sector string tables, built on the device with the combinatorial number
+ * system (§3.1 addressing).  Copies dim = C(norb, nocc) masks to
+ * `masks_host` (caller-owned, dim entries) in address order.
+ * Synchronous.  norb <= 32, dim < 2^31. */
+int fs_string_table(fs_ctx *ctx, int norb, int nocc, uint32_t *masks_host,
+                    int64_t dim);
+
+/* Single-excitation table for E_pq = a^dag_p a_q on strings of one spin
+ * (§2.2 sign convention).  For string address i and the pair (p, q):
+ * out[(i * norb + p) * norb + q] = (sign << 31) | target, where target is
+ * the address of I^{q->p} and sign = 1 when a^dag_p a_q |I> = -|I'>, or
+ * 0xFFFFFFFF when a^dag_p a_q |I> = 0.  For p == q the target is i and the
+ * sign is 0 when q is occupied.  `out_host` holds dim*norb*norb entries.
+ * Synchronous. */
+int fs_excitation_table(fs_ctx *ctx, int norb, int nocc, uint32_t *out_host,
+                        int64_t n_entries);
+
+/* Orbital rotation exp(sum_{pq sigma} log(U_sigma)_pq a^dag_{p sigma} a_{q sigma})
+ * (§2.3, §3.2.3, Table 1).  U_a and U_b are N x N unitary (host,
+ * complex); U_b == NULL means U_b = U_a.  `vec` is updated in place.
+ * Errors: FS_ERR_NOT_UNITARY when ||U^dag U - I||_max > 1e-10;
+ * FS_ERR_UNSUPPORTED when a string dimension exceeds 65535. */
+int fs_apply_orbital_rotation(fs_ctx *ctx, void *vec, int dtype,
+                              const double *U_a, const double *U_b, int norb,
+                              int n_alpha, int n_beta, void *stream);
+
+/* Number-operator-sum evolution exp(-i t sum_{p sigma} lambda^sigma_p n_{p sigma})
+ * (§3.2.1, Table 1).  lam_a, lam_b: N reals (host); lam_b == NULL means
+ * lam_b = lam_a. */
+int fs_apply_num_op_sum_evolution(fs_ctx *ctx, void *vec, int dtype,
+                                  const double *lam_a, const double *lam_b,
+                                  double t, int norb, int n_alpha, int n_beta,
+                                  void *stream);
+
+/* Diagonal-Coulomb evolution
+ *   exp(-1/2 i t sum_{pq sigma tau} J^{sigma tau}_pq n_{p sigma} n_{q tau})
+ * (§3.2.2, Table 1), J^{beta alpha} = (J^{alpha beta})^T.  J_aa, J_ab,
+ * J_bb: N x N reals (host); J_bb == NULL means J_bb = J_aa. */
+int fs_apply_diag_coulomb_evolution(fs_ctx *ctx, void *vec, int dtype,
+                                    const double *J_aa, const double *J_ab,
+                                    const double *J_bb, double t, int norb,
+                                    int n_alpha, int n_beta, void *stream);
+
+/* LUCJ ansatz (§4.3, §4.5.1): n_reps repetitions U_k D_k U_k^dag, k = 0 ..
+ * n_reps-1 applied in order, with U_k = U(expm(K_k)) (K_k anti-Hermitian,
+ * N x N complex) and D_k the spin-balanced diagonal-Coulomb evolution with
+ * J_bb = J_aa = J_aa[k], J_ab = J_ab[k] at t = 1.  No final rotation.
+ * K: n_reps*2*N*N doubles; J_aa, J_ab: n_reps*N*N doubles (host). */
+typedef struct {
+  int norb, n_alpha, n_beta, n_reps;
+  const double *K;
+  const double *J_aa;
+  const double *J_ab;
+  int from_hf; /* 1: start from the Hartree-Fock state, ignoring vec's input */
+} fs_lucj;
+
+/* vec: in = initial state (ignored when from_hf), out = final state. */
+int fs_lucj_forward(fs_ctx *ctx, const fs_lucj *op, void *vec, int dtype,
+                    void *stream);
+
+/* Vector-Jacobian product of the forward pass for L = Re <cot, psi_out>,
+ * by reverse sweeps that uncompute the state (no stored intermediates).
+ *   vec: in = psi_out (the forward result), out = the recomputed input state;
+ *   cot: in = dL/dpsi_out, out = dL/dpsi_in (conjugate-Wirtinger convention,
+ *        i.e. C^dag cot for the circuit C);
+ *   dK:   n_reps*2*N*N doubles, dL/dRe K + i dL/dIm K for every entry;
+ *   dJ_aa, dJ_ab: n_reps*N*N doubles, dL/dJ_pq with entries independent.
+ * Host outputs; synchronizes the stream.  Any of dK, dJ_aa, dJ_ab may be
+ * NULL to skip it. */
+int fs_lucj_vjp(fs_ctx *ctx, const fs_lucj *op, void *vec, void *cot,
+                int dtype, double *dK, double *dJ_aa, double *dJ_ab,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSGPU_H */

@@ -19,7 +19,8 @@ Slater-determinant closed form (§2.4), the group-homomorphism identities of
 from .strings import strings, address_map, occupations, excite
 from .gates import (dims, hartree_fock, apply_num_op_sum_evolution,
                     apply_diag_coulomb_evolution, diag_coulomb_angle,
-                    minor_matrix, apply_orbital_rotation,
+                    minor_matrix, minor_matrix_row, rotated_amplitude,
+                    apply_orbital_rotation,
                     apply_orbital_rotation_minors, apply_orbital_rotation_givens,
                     apply_givens, givens_matrix, givens_decomposition,
                     slater_from_hf)

@@ -101,6 +101,26 @@ def minor_matrix(U, norb, nocc):
     return M
 
 
+def minor_matrix_row(U, norb, nocc, a):
+    """Row `a` of the minor matrix: det(U[J_a, I]) for every string I."""
+    s = strings(norb, nocc)
+    if nocc == 0:
+        return np.ones(1, np.complex128)
+    occ = np.array([[p for p in range(norb) if (int(m) >> p) & 1] for m in s])
+    sub = np.asarray(U, complex)[occ[a], :]
+    return np.linalg.det(np.transpose(sub[:, occ], (1, 0, 2)))
+
+
+def rotated_amplitude(vec, U_a, U_b, norb, nelec, i, j):
+    """One amplitude of M_a vec M_b^T, for checks at sizes where the full
+    minor matrices are too large."""
+    if U_b is None:
+        U_b = U_a
+    ra = minor_matrix_row(U_a, norb, nelec[0], i)
+    rb = minor_matrix_row(U_b, norb, nelec[1], j)
+    return ra @ vec @ rb
+
+
 def apply_orbital_rotation_minors(vec, U_a, U_b, norb, nelec):
     """gamma' = M_a gamma M_b^T.  The alpha and beta one-body generators
     commute with each other and with the other spin's creation operators, so

@@ -1,0 +1,498 @@
+// C ABI of libfsgpu.so: argument checks, context and scratch management, and
+// the host-side orchestration of the kernels for each gate (§3.2) and for
+// the LUCJ ansatz (§4.3, §4.5.1).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+void* scratch(Ctx* ctx, const std::string& name, size_t bytes) {
+  Scratch& s = ctx->scratch[name];
+  if (s.bytes < bytes) {
+    if (s.ptr) FS_CUDA(cudaFree(s.ptr));
+    s.ptr = nullptr;
+    s.bytes = 0;
+    cudaError_t e = cudaMalloc(&s.ptr, bytes);
+    if (e != cudaSuccess) {
+      set_error("scratch allocation of " + std::to_string(bytes) + " bytes failed: " +
+                cudaGetErrorString(e));
+      throw Fail{FS_ERR_NOMEM};
+    }
+    s.bytes = bytes;
+  }
+  return s.ptr;
+}
+
+static std::vector<zd> load_cmat(const double* p, int n) {
+  std::vector<zd> m((size_t)n * n);
+  for (size_t k = 0; k < m.size(); ++k) m[k] = zd(p[2 * k], p[2 * k + 1]);
+  return m;
+}
+
+static void check_unitary(const std::vector<zd>& U, int n, const char* what) {
+  double e = unitarity_error(n, U.data());
+  FS_REQUIRE(e <= 1e-10, FS_ERR_NOT_UNITARY,
+             std::string(what) + " is not unitary (max |U^dag U - I| = " +
+                 std::to_string(e) + ")");
+}
+
+static void check_sector(Ctx* ctx, void* vec, int dtype, int norb, int na, int nb) {
+  FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+  FS_REQUIRE(dtype == FS_C64 || dtype == FS_C128, FS_ERR_ARG, "dtype must be FS_C64 or FS_C128");
+  FS_REQUIRE(norb >= 1 && norb <= kMaxNorb, FS_ERR_ARG, "norb must be in [1, 32]");
+  FS_REQUIRE(na >= 0 && na <= norb && nb >= 0 && nb <= norb, FS_ERR_ARG,
+             "electron counts must be in [0, norb]");
+  FS_REQUIRE(vec != nullptr, FS_ERR_ARG, "null state pointer");
+  FS_REQUIRE(((uintptr_t)vec & 15u) == 0, FS_ERR_ARG, "state pointer must be 16-byte aligned");
+}
+
+static Mat real_mat(const double* p, int n, double scale) {
+  Mat m;
+  for (int k = 0; k < n * n; ++k) m.v[k] = scale * p[k];
+  return m;
+}
+
+static StrPhase phase_of(const RotProgram* rp, const double* J, double t, const double* lam,
+                         int n) {
+  StrPhase f;
+  f.t = t;
+  if (rp) {
+    f.use_d = 1;
+    for (int p = 0; p < n; ++p) {
+      f.d[2 * p] = rp->phase[p].real();
+      f.d[2 * p + 1] = rp->phase[p].imag();
+    }
+  }
+  if (J) {
+    f.use_j = 1;
+    for (int k = 0; k < n * n; ++k) f.J.v[k] = J[k];
+  }
+  if (lam) {
+    f.use_lam = 1;
+    for (int p = 0; p < n; ++p) f.lam[p] = lam[p];
+  }
+  return f;
+}
+
+// A diagonal-Coulomb evolution fused into the epilogue of a beta sweep:
+// same-spin matrix J (J_bb = J_aa), mixed matrix J_ab, time t.
+struct Fused {
+  const double* J_aa = nullptr;  // host, N x N
+  const double* J_ab = nullptr;  // host, N x N
+  double t = 0;
+};
+
+// Orbital rotation with programs pa (alpha) and pb (beta): one sweep per
+// spin.  The beta sweep's epilogue also applies the optional fused
+// diagonal-Coulomb evolution `dc`.
+static void rotate(Ctx* ctx, Space* sa, Space* sb, void* v0, void* v1, int nst, int dtype,
+                   const RotProgram& pa, const RotProgram& pb, const Fused* dc,
+                   cudaStream_t st) {
+  const int n = sa->norb;
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  void* ea_a = scratch(ctx, "ea_a", sa->dim * csz);
+  void* ea_b = scratch(ctx, "ea_b", sb->dim * csz);
+  void* ea_o = scratch(ctx, "ea_o", sa->dim * csz);
+  launch_string_phase(sa, ea_a, dtype, phase_of(&pa, nullptr, 0, nullptr, n), st);
+  PhaseDev ph;
+  ph.ea_a = ea_a;
+  launch_sweep(ctx, sa, sb, 0, v0, v1, nst, dtype, pa, ph, st);
+  PhaseDev phb;
+  if (dc) {
+    launch_string_phase(sb, ea_b, dtype, phase_of(&pb, dc->J_aa, dc->t, nullptr, n), st);
+    launch_string_phase(sa, ea_o, dtype, phase_of(nullptr, dc->J_aa, dc->t, nullptr, n), st);
+    phb.ea_a = ea_o;
+    phb.has_x = 1;
+    // mixed terms (p in I_a, q in I_b) and (p in I_b, q in I_a), J_ba = J_ab^T
+    phb.X = real_mat(dc->J_ab, n, -dc->t);
+  } else {
+    launch_string_phase(sb, ea_b, dtype, phase_of(&pb, nullptr, 0, nullptr, n), st);
+  }
+  phb.ea_b = ea_b;
+  launch_sweep(ctx, sa, sb, 1, v0, v1, nst, dtype, pb, phb, st);
+}
+
+// Standalone diagonal phase pass (number-operator sum and/or diagonal Coulomb).
+static void phase_pass(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
+                       const StrPhase& fa, const StrPhase& fb, const double* J_ab,
+                       double xscale, cudaStream_t st) {
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  void* ea_a = scratch(ctx, "ea_a", sa->dim * csz);
+  void* ea_b = scratch(ctx, "ea_b", sb->dim * csz);
+  launch_string_phase(sa, ea_a, dtype, fa, st);
+  launch_string_phase(sb, ea_b, dtype, fb, st);
+  PhaseDev ph;
+  ph.ea_a = ea_a;
+  ph.ea_b = ea_b;
+  if (J_ab) {
+    ph.has_x = 1;
+    ph.X = real_mat(J_ab, sa->norb, xscale);
+  }
+  launch_phase(sa, sb, vec, dtype, ph, st);
+}
+
+template <class F>
+static int guarded(F&& f) {
+  try {
+    f();
+    return FS_OK;
+  } catch (Fail& e) {
+    return e.code;
+  } catch (std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FS_ERR_NOMEM;
+  } catch (std::exception& e) {
+    set_error(e.what());
+    return FS_ERR_ARG;
+  }
+}
+
+static void lucj_checks(Ctx* ctx, const fs_lucj* op, void* vec, int dtype) {
+  FS_REQUIRE(op != nullptr, FS_ERR_ARG, "null LUCJ operator");
+  check_sector(ctx, vec, dtype, op->norb, op->n_alpha, op->n_beta);
+  FS_REQUIRE(op->n_reps >= 0, FS_ERR_ARG, "n_reps must be >= 0");
+  FS_REQUIRE(op->n_reps == 0 || (op->K && op->J_aa && op->J_ab), FS_ERR_ARG,
+             "null LUCJ parameter array");
+}
+
+// Merged rotations of the LUCJ circuit: R_0 = U_0^dag, R_k = U_k^dag U_{k-1},
+// R_n = U_{n-1}, since U(A) U(B) = U(AB) (§2.3, merging as in §4.3).
+static std::vector<std::vector<zd>> lucj_rotations(const fs_lucj* op,
+                                                   std::vector<std::vector<zd>>* Us_out) {
+  const int n = op->norb, R = op->n_reps;
+  const size_t nn = (size_t)n * n;
+  std::vector<std::vector<zd>> Us(R), Rs(R + 1, std::vector<zd>(nn));
+  for (int k = 0; k < R; ++k) {
+    std::vector<zd> K = load_cmat(op->K + 2 * nn * k, n);
+    Us[k].resize(nn);
+    expm(n, K.data(), Us[k].data());
+  }
+  std::vector<zd> adj(nn);
+  mat_adjoint(n, Us[0].data(), Rs[0].data());
+  for (int k = 1; k < R; ++k) {
+    mat_adjoint(n, Us[k].data(), adj.data());
+    mat_mul(n, adj.data(), Us[k - 1].data(), Rs[k].data());
+  }
+  Rs[R] = Us[R - 1];
+  if (Us_out) *Us_out = Us;
+  return Rs;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+struct fs_ctx : public fs::Ctx {};
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_err.c_str(); }
+
+int fs_create(fs_ctx** out, int device) {
+  return guarded([&] {
+    FS_REQUIRE(out != nullptr, FS_ERR_ARG, "null output pointer");
+    int n = 0;
+    FS_CUDA(cudaGetDeviceCount(&n));
+    FS_REQUIRE(device >= 0 && device < n, FS_ERR_ARG, "device index out of range");
+    FS_CUDA(cudaSetDevice(device));
+    fs_ctx* c = new fs_ctx();
+    c->device = device;
+    FS_CUDA(cudaGetDeviceProperties(&c->prop, device));
+    FS_CUDA(cudaMalloc(&c->d_status, sizeof(int)));
+    FS_CUDA(cudaMemset(c->d_status, 0, sizeof(int)));
+    *out = c;
+  });
+}
+
+int fs_destroy(fs_ctx* ctx) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    FS_CUDA(cudaSetDevice(ctx->device));
+    FS_CUDA(cudaDeviceSynchronize());
+    for (auto& kv : ctx->spaces) free_space(kv.second);
+    for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
+    cudaFree(ctx->d_status);
+    delete ctx;
+  });
+}
+
+int fs_sync_status(fs_ctx* ctx, void* stream) {
+  int code = 0;
+  int rc = guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    cudaStream_t st = (cudaStream_t)stream;
+    FS_CUDA(cudaMemcpyAsync(&code, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+    FS_CUDA(cudaStreamSynchronize(st));
+  });
+  if (rc != FS_OK) return rc;
+  if (code != 0) set_error("device status word reported an error");
+  return code;
+}
+
+int fs_set_rotation_path(fs_ctx* ctx, int path) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    FS_REQUIRE(path >= FS_ROT_AUTO && path <= FS_ROT_MINORS, FS_ERR_ARG, "unknown rotation path");
+    ctx->rot_path = path;
+  });
+}
+
+int fs_string_table(fs_ctx* ctx, int norb, int nocc, uint32_t* masks_host, int64_t dim) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr && masks_host != nullptr, FS_ERR_ARG, "null pointer");
+    FS_REQUIRE(norb >= 0 && norb <= kMaxNorb && nocc >= 0 && nocc <= norb, FS_ERR_ARG,
+               "bad (norb, nocc)");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    Space* s = get_space(ctx, norb, nocc, 0);
+    FS_REQUIRE(dim == s->dim, FS_ERR_ARG, "dim must equal C(norb, nocc)");
+    FS_CUDA(cudaMemcpy(masks_host, s->masks, dim * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int fs_excitation_table(fs_ctx* ctx, int norb, int nocc, uint32_t* out_host, int64_t n) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr && out_host != nullptr, FS_ERR_ARG, "null pointer");
+    FS_REQUIRE(norb >= 1 && norb <= kMaxNorb && nocc >= 0 && nocc <= norb, FS_ERR_ARG,
+               "bad (norb, nocc)");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    Space* s = get_space(ctx, norb, nocc, 0);
+    FS_REQUIRE(n == s->dim * norb * norb, FS_ERR_ARG, "n_entries must be dim*norb*norb");
+    uint32_t* d = (uint32_t*)scratch(ctx, "exc", n * 4);
+    launch_exc_table(s, d, 0);
+    FS_CUDA(cudaMemcpy(out_host, d, n * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int fs_apply_orbital_rotation(fs_ctx* ctx, void* vec, int dtype, const double* U_a,
+                              const double* U_b, int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    FS_REQUIRE(U_a != nullptr, FS_ERR_ARG, "null U_a");
+    std::vector<zd> Ua = load_cmat(U_a, norb);
+    std::vector<zd> Ub = U_b ? load_cmat(U_b, norb) : Ua;
+    check_unitary(Ua, norb, "U_a");
+    if (U_b) check_unitary(Ub, norb, "U_b");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    RotProgram pa = decompose_adjacent(norb, Ua.data());
+    RotProgram pb = U_b ? decompose_adjacent(norb, Ub.data()) : pa;
+    rotate(ctx, sa, sb, vec, nullptr, 1, dtype, pa, pb, nullptr, st);
+  });
+}
+
+int fs_apply_num_op_sum_evolution(fs_ctx* ctx, void* vec, int dtype, const double* lam_a,
+                                  const double* lam_b, double t, int norb, int na, int nb,
+                                  void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    FS_REQUIRE(lam_a != nullptr, FS_ERR_ARG, "null lam_a");
+    FS_REQUIRE(std::isfinite(t), FS_ERR_ARG, "t must be finite");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, nullptr, t, lam_a, norb),
+               phase_of(nullptr, nullptr, t, lam_b ? lam_b : lam_a, norb), nullptr, 0, st);
+  });
+}
+
+int fs_apply_diag_coulomb_evolution(fs_ctx* ctx, void* vec, int dtype, const double* J_aa,
+                                    const double* J_ab, const double* J_bb, double t,
+                                    int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    FS_REQUIRE(J_aa != nullptr && J_ab != nullptr, FS_ERR_ARG, "null J_aa or J_ab");
+    FS_REQUIRE(std::isfinite(t), FS_ERR_ARG, "t must be finite");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    // theta = -(t/2)[sum_{I_a} J_aa + sum_{I_b} J_bb + 2 sum_{p in I_a, q in I_b} J_ab]
+    phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, J_aa, t, nullptr, norb),
+               phase_of(nullptr, J_bb ? J_bb : J_aa, t, nullptr, norb), J_ab, -t, st);
+  });
+}
+
+int fs_lucj_forward(fs_ctx* ctx, const fs_lucj* op, void* vec, int dtype, void* stream) {
+  return guarded([&] {
+    lucj_checks(ctx, op, vec, dtype);
+    const int n = op->norb, R = op->n_reps;
+    const size_t nn = (size_t)n * n;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, n, op->n_alpha, st);
+    Space* sb = get_space(ctx, n, op->n_beta, st);
+    if (R == 0) {
+      if (op->from_hf) {
+        CMat I{};
+        for (int p = 0; p < n; ++p) I.v[2 * (p * n + p)] = 1.0;
+        launch_slater(ctx, sa, sb, vec, dtype, I, st);
+      }
+      return;
+    }
+    auto Rs = lucj_rotations(op, nullptr);
+    int k0 = 0;
+    if (op->from_hf) {
+      // U(R_0)|HF> is a Slater determinant: rank-1 closed form (§2.4)
+      CMat Rm{};
+      for (size_t q = 0; q < nn; ++q) {
+        Rm.v[2 * q] = Rs[0][q].real();
+        Rm.v[2 * q + 1] = Rs[0][q].imag();
+      }
+      launch_slater(ctx, sa, sb, vec, dtype, Rm, st);
+      phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, op->J_aa, 1.0, nullptr, n),
+                 phase_of(nullptr, op->J_aa, 1.0, nullptr, n), op->J_ab, -1.0, st);
+      k0 = 1;
+    }
+    for (int k = k0; k <= R; ++k) {
+      RotProgram p = decompose_adjacent(n, Rs[k].data());
+      if (k < R) {
+        Fused dc;
+        dc.J_aa = op->J_aa + k * nn;
+        dc.J_ab = op->J_ab + k * nn;
+        dc.t = 1.0;
+        rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, &dc, st);
+      } else {
+        rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, nullptr, st);
+      }
+    }
+  });
+}
+
+}  // extern "C"
+
+namespace fs {
+
+// Reverse sweeps over the merged LUCJ circuit
+//   psi_out = U(R_n) D_{n-1} U(R_{n-1}) ... D_0 U(R_0) psi_in.
+// For m = n .. 0: undo U(R_m) on psi and g together (beta sweep, then alpha
+// sweep), accumulating T^(m)_pq = <g| E_pq |psi> at the input side of U(R_m);
+// the alpha sweep also writes W = Im(conj(g) psi) and undoes D_{m-1}.
+// With dL = Re sum (R^-1 dR)_pq T_pq, the Euclidean gradient is R conj(T);
+// the chain rule through R_m = U_m^dag U_{m-1} and K -> expm(K) is FP64 host
+// work.
+static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int dtype,
+                          double* dK, double* dJ_aa, double* dJ_ab, cudaStream_t st) {
+  const int n = op->norb, R = op->n_reps;
+  const size_t nn = (size_t)n * n;
+  Space* sa = get_space(ctx, n, op->n_alpha, st);
+  Space* sb = get_space(ctx, n, op->n_beta, st);
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  if (R == 0) {
+    if (dK || dJ_aa || dJ_ab) FS_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
+  std::vector<std::vector<zd>> Us;
+  auto Rs = lucj_rotations(op, &Us);
+  double* Tacc = (double*)scratch(ctx, "vjp_T", (R + 1) * nn * 2 * sizeof(double));
+  double* dJd = (double*)scratch(ctx, "vjp_dJ", 2 * R * nn * sizeof(double));
+  FS_CUDA(cudaMemsetAsync(Tacc, 0, (R + 1) * nn * 2 * sizeof(double), st));
+  FS_CUDA(cudaMemsetAsync(dJd, 0, 2 * R * nn * sizeof(double), st));
+  double* dJaa_d = dJd;
+  double* dJab_d = dJd + R * nn;
+  void* Wb = scratch(ctx, "vjp_W", sa->dim * sb->dim * (csz / 2));
+  void* ea_a = scratch(ctx, "ea_a", sa->dim * csz);
+  void* ea_b = scratch(ctx, "ea_b", sb->dim * csz);
+  void* e2_a = scratch(ctx, "ea2_a", sa->dim * csz);
+  void* e2_b = scratch(ctx, "ea2_b", sb->dim * csz);
+  std::vector<zd> adj(nn);
+  for (int m = R; m >= 0; --m) {
+    mat_adjoint(n, Rs[m].data(), adj.data());
+    RotProgram inv = decompose_adjacent(n, adj.data());
+    double* Tm = Tacc + (size_t)m * nn * 2;
+    // beta: undo, T^beta
+    launch_string_phase(sb, ea_b, dtype, phase_of(&inv, nullptr, 0, nullptr, n), st);
+    PhaseDev p1;
+    p1.ea_b = ea_b;
+    RevArgs r1;
+    r1.T = Tm;
+    launch_sweep(ctx, sa, sb, 1, vec, cot, 2, dtype, inv, p1, st, &r1);
+    // alpha: undo, T^alpha, W and D_{m-1}^dag
+    launch_string_phase(sa, ea_a, dtype, phase_of(&inv, nullptr, 0, nullptr, n), st);
+    PhaseDev p2;
+    p2.ea_a = ea_a;
+    RevArgs r2;
+    r2.T = Tm;
+    if (m >= 1) {
+      const double* Ja = op->J_aa + (size_t)(m - 1) * nn;
+      launch_string_phase(sa, e2_a, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
+      launch_string_phase(sb, e2_b, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
+      r2.ea2_a = e2_a;
+      r2.ea2_b = e2_b;
+      r2.W = Wb;
+      p2.has_x = 1;
+      p2.X = real_mat(op->J_ab + (size_t)(m - 1) * nn, n, 1.0);
+    }
+    launch_sweep(ctx, sa, sb, 0, vec, cot, 2, dtype, inv, p2, st, &r2);
+    if (m >= 1)
+      launch_dc_grad(ctx, sa, sb, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
+                     dJab_d + (size_t)(m - 1) * nn, st);
+  }
+  std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn);
+  FS_CUDA(cudaMemcpyAsync(Th.data(), Tacc, Th.size() * 8, cudaMemcpyDeviceToHost, st));
+  FS_CUDA(cudaMemcpyAsync(dJh.data(), dJd, dJh.size() * 8, cudaMemcpyDeviceToHost, st));
+  FS_CUDA(cudaStreamSynchronize(st));
+  if (dJ_aa) std::copy(dJh.begin(), dJh.begin() + R * nn, dJ_aa);
+  if (dJ_ab) std::copy(dJh.begin() + R * nn, dJh.end(), dJ_ab);
+  if (!dK) return;
+  std::vector<std::vector<zd>> gU(R, std::vector<zd>(nn, zd(0)));
+  std::vector<zd> gR(nn), cT(nn), tmp(nn), tmp2(nn);
+  for (int m = 0; m <= R; ++m) {
+    for (size_t q = 0; q < nn; ++q)
+      cT[q] = zd(Th[2 * (m * nn + q)], -Th[2 * (m * nn + q) + 1]);
+    mat_mul(n, Rs[m].data(), cT.data(), gR.data());  // R conj(T)
+    if (m == 0) {
+      mat_adjoint(n, gR.data(), tmp.data());
+      for (size_t q = 0; q < nn; ++q) gU[0][q] += tmp[q];
+    }
+    if (m == R) {
+      for (size_t q = 0; q < nn; ++q) gU[R - 1][q] += gR[q];
+    }
+    if (m >= 1 && m <= R - 1) {
+      mat_mul(n, Us[m].data(), gR.data(), tmp.data());
+      for (size_t q = 0; q < nn; ++q) gU[m - 1][q] += tmp[q];
+      mat_adjoint(n, gR.data(), tmp2.data());
+      mat_mul(n, Us[m - 1].data(), tmp2.data(), tmp.data());
+      for (size_t q = 0; q < nn; ++q) gU[m][q] += tmp[q];
+    }
+  }
+  for (int k = 0; k < R; ++k) {
+    std::vector<zd> K = load_cmat(op->K + 2 * nn * k, n), out(nn);
+    expm_frechet_adjoint(n, K.data(), gU[k].data(), out.data());
+    for (size_t q = 0; q < nn; ++q) {
+      dK[2 * (k * nn + q)] = out[q].real();
+      dK[2 * (k * nn + q) + 1] = out[q].imag();
+    }
+  }
+}
+
+}  // namespace fs
+
+extern "C" int fs_lucj_vjp(fs_ctx* ctx, const fs_lucj* op, void* vec, void* cot, int dtype,
+                           double* dK, double* dJ_aa, double* dJ_ab, void* stream) {
+  return guarded([&] {
+    lucj_checks(ctx, op, vec, dtype);
+    FS_REQUIRE(cot != nullptr && ((uintptr_t)cot & 15u) == 0, FS_ERR_ARG,
+               "cotangent pointer must be non-null and 16-byte aligned");
+    FS_REQUIRE(cot != vec, FS_ERR_ARG, "state and cotangent must be distinct buffers");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    FS_CUDA(cudaSetDevice(ctx->device));
+    lucj_vjp_impl(ctx, op, vec, cot, dtype, dK, dJ_aa, dJ_ab, (cudaStream_t)stream);
+  });
+}

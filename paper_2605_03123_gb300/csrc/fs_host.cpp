@@ -1,0 +1,137 @@
+// Host-side FP64 linear algebra for fsgpu: matrix exponential and the adjoint
+// of its Frechet derivative, unitarity checks, and the adjacent-pair Givens
+// decomposition of an orbital-rotation matrix (§3.2.3).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+void mat_mul(int n, const zd* A, const zd* B, zd* C) {
+  std::vector<zd> t((size_t)n * n, zd(0));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      zd a = A[i * n + k];
+      if (a == zd(0)) continue;
+      for (int j = 0; j < n; ++j) t[i * n + j] += a * B[k * n + j];
+    }
+  std::copy(t.begin(), t.end(), C);
+}
+
+void mat_adjoint(int n, const zd* A, zd* out) {
+  std::vector<zd> t((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) t[j * n + i] = std::conj(A[i * n + j]);
+  std::copy(t.begin(), t.end(), out);
+}
+
+static double norm1(int n, const zd* A) {
+  double m = 0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += std::abs(A[i * n + j]);
+    m = std::max(m, s);
+  }
+  return m;
+}
+
+// Scaling and squaring with a Taylor series: A / 2^s has 1-norm <= 1/2, and
+// the series is summed until a term no longer changes the sum in FP64.
+void expm(int n, const zd* A, zd* out) {
+  const size_t nn = (size_t)n * n;
+  double nrm = norm1(n, A);
+  int s = 0;
+  if (nrm > 0.5) s = (int)std::ceil(std::log2(nrm / 0.5));
+  double scale = std::ldexp(1.0, -s);
+  std::vector<zd> B(nn), term(nn), sum(nn, zd(0)), tmp(nn);
+  for (size_t k = 0; k < nn; ++k) B[k] = A[k] * scale;
+  for (int i = 0; i < n; ++i) {
+    sum[i * n + i] = 1.0;
+    term[i * n + i] = 1.0;
+  }
+  for (int k = 1; k <= 40; ++k) {
+    mat_mul(n, term.data(), B.data(), tmp.data());
+    double tn = 0;
+    for (size_t q = 0; q < nn; ++q) {
+      term[q] = tmp[q] / (double)k;
+      sum[q] += term[q];
+      tn = std::max(tn, std::abs(term[q]));
+    }
+    if (tn < 1e-18) break;
+  }
+  for (int k = 0; k < s; ++k) mat_mul(n, sum.data(), sum.data(), sum.data());
+  std::copy(sum.begin(), sum.end(), out);
+}
+
+// For the real inner product <A, B> = Re tr(A^dag B), the adjoint of the
+// Frechet derivative of expm at K is the Frechet derivative at K^dag; the
+// latter is the upper-right block of expm([[K^dag, H], [0, K^dag]]).
+void expm_frechet_adjoint(int n, const zd* K, const zd* H, zd* out) {
+  const int m = 2 * n;
+  std::vector<zd> B((size_t)m * m, zd(0)), E((size_t)m * m);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      zd kd = std::conj(K[j * n + i]);
+      B[i * m + j] = kd;
+      B[(n + i) * m + n + j] = kd;
+      B[i * m + n + j] = H[i * n + j];
+    }
+  expm(m, B.data(), E.data());
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) out[i * n + j] = E[i * m + n + j];
+}
+
+double unitarity_error(int n, const zd* U) {
+  double e = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      zd s = 0;
+      for (int k = 0; k < n; ++k) s += std::conj(U[k * n + i]) * U[k * n + j];
+      if (i == j) s -= 1.0;
+      e = std::max(e, std::abs(s));
+    }
+  return e;
+}
+
+// Column elimination by adjacent Givens rotations from the right: for rows
+// r = N-1 .. 1 and columns j = 0 .. r-1, a rotation on columns (j, j+1)
+// zeroes A[r][j] and carries the row's weight to column j+1.  With
+// A <- A G^dag and G = [[c, s], [-s*, c]] on (j, j+1):
+//   new A[r][j] = c a + s* b = 0 for c = |b|/rho, s = -conj(a) b / (|b| rho).
+// After all rows A is diagonal: U G_1^dag ... G_M^dag = D, so
+// U = D G_M ... G_1 and the operator of G_1 acts first.
+RotProgram decompose_adjacent(int n, const zd* U) {
+  std::vector<zd> A(U, U + (size_t)n * n);
+  RotProgram prog;
+  for (int r = n - 1; r >= 1; --r) {
+    for (int j = 0; j < r; ++j) {
+      zd a = A[r * n + j], b = A[r * n + j + 1];
+      if (std::abs(a) == 0.0) continue;  // already zero: identity rotation
+      double c;
+      zd s;
+      if (std::abs(b) == 0.0) {  // swap-like rotation: c = 0, s = -conj(a)/|a|
+        c = 0.0;
+        s = -std::conj(a) / std::abs(a);
+      } else {
+        double rho = std::hypot(std::abs(a), std::abs(b));
+        c = std::abs(b) / rho;
+        s = -std::conj(a) * b / (std::abs(b) * rho);
+      }
+      // A <- A G^dag on columns (j, j+1): G^dag = [[c, -s], [s*, c]]
+      for (int i = 0; i < n; ++i) {
+        zd x = A[i * n + j], y = A[i * n + j + 1];
+        A[i * n + j] = c * x + std::conj(s) * y;
+        A[i * n + j + 1] = -s * x + c * y;
+      }
+      A[r * n + j] = 0.0;
+      prog.g.push_back(Givens{j, c, s});
+    }
+  }
+  prog.phase.resize(n);
+  for (int i = 0; i < n; ++i) prog.phase[i] = A[i * n + i];
+  return prog;
+}
+
+}  // namespace fs

@@ -1,0 +1,173 @@
+// Internal declarations shared by the fsgpu translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fsgpu.h"
+
+namespace fs {
+
+using zd = std::complex<double>;
+
+// Largest orbital count handled by the string tables (masks are uint32).
+constexpr int kMaxNorb = 32;
+constexpr int kMaxOrb = kMaxNorb;
+// Largest number of Givens rotations in one program: N(N-1)/2 for N = 32.
+constexpr int kMaxGivens = kMaxNorb * (kMaxNorb - 1) / 2;
+// Vector length limit of the sweep kernels (16-bit addresses in pair lists).
+constexpr int64_t kMaxSweepDim = 65535;
+
+// ------------------------------------------------------------- host math
+// One adjacent-pair Givens rotation G = [[c, s], [-s*, c]] on orbitals
+// (p, p+1).
+struct Givens {
+  int p;
+  double c;
+  zd s;
+};
+// U = D * G_M ... G_1 with D = diag(phase): G_1 acts first on the state.
+struct RotProgram {
+  std::vector<Givens> g;
+  std::vector<zd> phase;
+};
+
+void mat_mul(int n, const zd* A, const zd* B, zd* C);            // C = A B
+void mat_adjoint(int n, const zd* A, zd* out);                   // out = A^dag
+void expm(int n, const zd* A, zd* out);                          // FP64
+void expm_frechet_adjoint(int n, const zd* K, const zd* H, zd* out);
+double unitarity_error(int n, const zd* U);
+RotProgram decompose_adjacent(int n, const zd* U);
+
+// ------------------------------------------------------ device tables
+// Per-sector-spin tables: strings of `nocc` electrons in `norb` orbitals.
+struct Space {
+  int norb = 0, nocc = 0;
+  int64_t dim = 0;
+  uint32_t* masks = nullptr;  // [dim] string masks in address order
+  uint32_t* pairs = nullptr;  // [(norb-1) * npp]: adjacent Givens pair lists
+  int npp = 0;                // C(norb-2, nocc-1) pairs per adjacent (p, p+1)
+  // pair lists for all ordered (p, q), p != q, and the diagonal lists, used by
+  // the transition one-body reductions
+  uint32_t* xpairs = nullptr;  // [norb*norb][nx] packed (src | dst << 16)
+  uint32_t* xsign = nullptr;   // [norb*norb][ceil(nx/32)] sign bits
+  int nx = 0;                  // entries per (p, q) list (max over p, q)
+  int* xcount = nullptr;       // [norb*norb] actual entries per list
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaDeviceProp prop{};
+  int rot_path = FS_ROT_AUTO;
+  std::map<std::pair<int, int>, Space*> spaces;
+  std::map<std::string, Scratch> scratch;
+  int* d_status = nullptr;  // device status word
+  std::mutex mu;
+};
+
+Space* get_space(Ctx* ctx, int norb, int nocc, cudaStream_t st);
+void free_space(Space* s);
+void* scratch(Ctx* ctx, const std::string& name, size_t bytes);
+
+// ------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+struct Fail {
+  int code;
+};
+#define FS_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      ::fs::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));     \
+      throw ::fs::Fail{FS_ERR_CUDA};                                           \
+    }                                                                          \
+  } while (0)
+#define FS_REQUIRE(cond, code, msg)    \
+  do {                                 \
+    if (!(cond)) {                     \
+      ::fs::set_error(msg);            \
+      throw ::fs::Fail{code};          \
+    }                                  \
+  } while (0)
+
+// ------------------------------------------------------ kernel launchers
+// Small matrices travel to the kernels by value, as kernel parameters.
+struct Mat {
+  double v[kMaxOrb * kMaxOrb];
+};
+struct CMat {
+  double v[2 * kMaxOrb * kMaxOrb];
+};
+struct StrPhase {  // per-string factor recipe, see launch_string_phase
+  int use_d = 0, use_j = 0, use_lam = 0;
+  double t = 0;
+  double d[2 * kMaxOrb];
+  double lam[kMaxOrb];
+  Mat J;
+};
+
+// Phase of one configuration, factored as
+//   f(i, j) = ea_a[i] * ea_b[j] * exp(i sum_{p in I_a, q in I_b} X[p][q])
+// with per-string factor tables ea_* (device, may be null = 1) and a real
+// cross matrix X (unused when has_x == 0).
+struct PhaseDev {
+  const void* ea_a = nullptr;
+  const void* ea_b = nullptr;
+  int has_x = 0;
+  Mat X;
+};
+
+// Per-string factors: out[e] = prod_{p in I} d_p * exp(i(-(t/2) sum_{p,q in I} J[p][q]
+//                                                    - t sum_{p in I} lam[p])).
+void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& f,
+                         cudaStream_t st);
+
+// Reverse-mode extras of a dual-state sweep (st0 = psi, st1 = cotangent).
+struct RevArgs {
+  const void* ea2_a = nullptr;  // second phase, applied after the reductions
+  const void* ea2_b = nullptr;
+  double* T = nullptr;  // [norb][norb] complex, += <g| E_pq |psi> (this spin)
+  void* W = nullptr;    // [d_a][d_b] real Im(conj(g) psi), or null
+};
+
+// Givens sweep over one spin: dir 0 rotates alpha (columns of the state),
+// dir 1 rotates beta (rows).  With nst == 1 the epilogue multiplies by the
+// phase `ph` (strings of both spins, cross matrix ph.X).  With nst == 2
+// (reverse mode, `rev` required) both states get the program, then the
+// per-string factors of `ph` (no cross term), then the reductions of `rev`,
+// then the phase rev->ea2_* times the cross term ph.X.
+void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir,
+                  void* st0, void* st1, int nst, int dtype,
+                  const RotProgram& prog, const PhaseDev& ph, cudaStream_t st,
+                  const RevArgs* rev = nullptr);
+
+// dJ from W = Im(conj(g) psi) of one diagonal-Coulomb gate (t = 1):
+//   dJ_ab[p][q] += sum_{ij} W_ij occ_a(i)_p occ_b(j)_q
+//   dJ_aa[p][q] += 1/2 sum_{ij} W_ij (occ_a(i)_p occ_a(i)_q + occ_b(j)_p occ_b(j)_q)
+// dJ_aa, dJ_ab: device [norb][norb] FP64 accumulators.
+void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,
+                    double* dJ_aa, double* dJ_ab, cudaStream_t st);
+
+// Multiply the state by the phase `ph` (one streaming pass).
+void launch_phase(const Space* sa, const Space* sb, void* vec, int dtype,
+                  const PhaseDev& ph, cudaStream_t st);
+
+// Hartree-Fock closed form (§2.4): psi[i][j] = det(R[I_a(i), 0..n_a-1]) *
+// det(R[I_b(j), 0..n_b-1]) for the N x N matrix R, computed in FP64.
+void launch_slater(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dtype,
+                   const CMat& R, cudaStream_t st);
+
+void launch_exc_table(const Space* sp, uint32_t* out, cudaStream_t st);
+
+}  // namespace fs

@@ -1,0 +1,145 @@
+// Gradient of a diagonal-Coulomb gate with respect to its coupling matrices.
+//
+// For D = exp(i theta) with theta = -1/2 [occ_a^T J_aa occ_a + occ_b^T J_aa
+// occ_b + 2 occ_a^T J_ab occ_b] (§3.2.2, spin-balanced, t = 1) and a loss
+// L = Re <g, D psi>, dL/dtheta_ij = -W_ij with W = Im(conj(g) D psi), so
+//   dL/dJ_ab = Occ_a^T W Occ_b,
+//   dL/dJ_aa = 1/2 (Occ_a^T diag(W 1) Occ_a + Occ_b^T diag(W^T 1) Occ_b).
+// W is written by the reverse-mode sweep; these kernels reduce it.
+#include <algorithm>
+
+#include "fs_common.cuh"
+#include "fs_internal.h"
+
+namespace fs {
+
+constexpr int kRThreads = 256;
+
+// Rows: V_i[q] = sum_j W_ij occ_b(j)_q and r_i = sum_j W_ij; then
+// dJ_ab[p][q] += occ_a(i)_p V_i[q] and dJ_aa[p][q] += 1/2 r_i occ_a(i)_p occ_a(i)_q,
+// accumulated per CTA in shared memory and flushed once.
+template <typename R, int NQ>
+__global__ void __launch_bounds__(kRThreads)
+    k_dc_rows(const R* W, int64_t da, int64_t db, const uint32_t* ma, const uint32_t* mb,
+              int norb, double* dJaa, double* dJab) {
+  __shared__ double sab[kMaxOrb * kMaxOrb], saa[kMaxOrb * kMaxOrb];
+  __shared__ double red[kRThreads / 32][NQ + 1];
+  for (int k = threadIdx.x; k < norb * norb; k += kRThreads) sab[k] = saa[k] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < da; i += gridDim.x) {
+    double acc[NQ];
+    double r = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0;
+    const R* row = W + i * db;
+    for (int64_t j = threadIdx.x; j < db; j += kRThreads) {
+      double w = (double)row[j];
+      uint32_t m = __ldg(mb + j);
+      r += w;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] += ((m >> q) & 1u) ? w : 0.0;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] += __shfl_xor_sync(0xFFFFFFFFu, acc[q], off);
+    }
+    if (lane == 0) {
+      red[wid][NQ] = r;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) red[wid][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < norb + 1) {
+      double s = 0;
+      const int q = threadIdx.x < norb ? threadIdx.x : NQ;
+      for (int k = 0; k < kRThreads / 32; ++k) s += red[k][q];
+      red[0][q] = s;  // safe: each q column is owned by one thread
+    }
+    __syncthreads();
+    uint32_t mi = ma[i];
+    const double ri = red[0][NQ];
+    for (int k = threadIdx.x; k < norb * norb; k += kRThreads) {
+      int p = k / norb, q = k - p * norb;
+      if ((mi >> p) & 1u) {
+        sab[k] += red[0][q];
+        if ((mi >> q) & 1u) saa[k] += 0.5 * ri;
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < norb * norb; k += kRThreads) {
+    if (sab[k] != 0) atomicAdd(dJab + k, sab[k]);
+    if (saa[k] != 0) atomicAdd(dJaa + k, saa[k]);
+  }
+}
+
+// Columns: c_j = sum_i W_ij over a chunk of rows, accumulated atomically.
+template <typename R>
+__global__ void k_dc_cols(const R* W, int64_t da, int64_t db, int rows_per, double* c) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= db) return;
+  int64_t i0 = (int64_t)blockIdx.y * rows_per, i1 = min(da, i0 + rows_per);
+  double s = 0;
+  for (int64_t i = i0; i < i1; ++i) s += (double)W[i * db + j];
+  atomicAdd(c + j, s);
+}
+
+// dJ_aa[p][q] += 1/2 sum_j c_j occ_b(j)_p occ_b(j)_q.
+__global__ void __launch_bounds__(kRThreads)
+    k_dc_beta_aa(const double* c, int64_t db, const uint32_t* mb, int norb, double* dJaa) {
+  __shared__ double s[kMaxOrb * kMaxOrb];
+  for (int k = threadIdx.x; k < norb * norb; k += kRThreads) s[k] = 0;
+  __syncthreads();
+  for (int64_t j = blockIdx.x * (int64_t)kRThreads + threadIdx.x; j < db;
+       j += (int64_t)gridDim.x * kRThreads) {
+    uint32_t m = mb[j];
+    double v = 0.5 * c[j];
+    for (uint32_t a = m; a; a &= a - 1) {
+      int p = __ffs(a) - 1;
+      for (uint32_t b = m; b; b &= b - 1) atomicAdd(&s[p * norb + __ffs(b) - 1], v);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < norb * norb; k += kRThreads)
+    if (s[k] != 0) atomicAdd(dJaa + k, s[k]);
+}
+
+void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,
+                    double* dJ_aa, double* dJ_ab, cudaStream_t st) {
+  const int norb = sa->norb;
+  const int sms = ctx->prop.multiProcessorCount;
+  unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 2 * sms);
+  if (dtype == FS_C64) {
+    if (norb <= 16)
+      k_dc_rows<float, 16><<<grid, kRThreads, 0, st>>>((const float*)W, sa->dim, sb->dim,
+                                                       sa->masks, sb->masks, norb, dJ_aa, dJ_ab);
+    else
+      k_dc_rows<float, 32><<<grid, kRThreads, 0, st>>>((const float*)W, sa->dim, sb->dim,
+                                                       sa->masks, sb->masks, norb, dJ_aa, dJ_ab);
+  } else {
+    if (norb <= 16)
+      k_dc_rows<double, 16><<<grid, kRThreads, 0, st>>>((const double*)W, sa->dim, sb->dim,
+                                                        sa->masks, sb->masks, norb, dJ_aa, dJ_ab);
+    else
+      k_dc_rows<double, 32><<<grid, kRThreads, 0, st>>>((const double*)W, sa->dim, sb->dim,
+                                                        sa->masks, sb->masks, norb, dJ_aa, dJ_ab);
+  }
+  FS_CUDA(cudaGetLastError());
+  double* c = (double*)scratch(ctx, "dc_colsum", sb->dim * sizeof(double));
+  FS_CUDA(cudaMemsetAsync(c, 0, sb->dim * sizeof(double), st));
+  const int rows_per = 256;
+  dim3 g2((unsigned)((sb->dim + 255) / 256), (unsigned)((sa->dim + rows_per - 1) / rows_per));
+  if (dtype == FS_C64)
+    k_dc_cols<float><<<g2, 256, 0, st>>>((const float*)W, sa->dim, sb->dim, rows_per, c);
+  else
+    k_dc_cols<double><<<g2, 256, 0, st>>>((const double*)W, sa->dim, sb->dim, rows_per, c);
+  FS_CUDA(cudaGetLastError());
+  unsigned g3 = (unsigned)std::min<int64_t>((sb->dim + kRThreads - 1) / kRThreads, sms);
+  k_dc_beta_aa<<<g3, kRThreads, 0, st>>>(c, sb->dim, sb->masks, norb, dJ_aa);
+  FS_CUDA(cudaGetLastError());
+}
+
+}  // namespace fs

@@ -1,0 +1,609 @@
+// Givens-rotation sweeps and per-configuration phases.
+//
+// An orbital rotation of one spin acts on every "vector" of the state that
+// holds all strings of that spin: the columns for alpha (dir 0), the rows
+// for beta (dir 1).  A slab of KV such vectors is staged in shared memory
+// (split over a thread-block cluster when one vector exceeds one SM's shared
+// memory), every Givens rotation of the program is applied to it in order
+// (§3.2.3: each rotation updates the amplitude pairs (I, I^{p->p+1})), and
+// the slab is written back once, multiplied by the configuration phases
+// (the diagonal layer of the decomposition, and optionally a fused
+// diagonal-Coulomb / number-operator evolution, §3.2.1-§3.2.2).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "fs_common.cuh"
+#include "fs_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace fs {
+
+constexpr int kThreads = 512;
+constexpr int kMaxKV = 64;
+
+template <typename R>
+struct GProg {
+  int m;
+  int8_t p[kMaxGivens];
+  R c[kMaxGivens];
+  R sr[kMaxGivens];
+  R si[kMaxGivens];
+};
+
+struct SweepGeom {
+  void* st[2];
+  int64_t d_b;  // row stride of the state
+  int dir;      // 0: alpha, vectors are columns; 1: beta, vectors are rows
+  int d;        // vector length (strings of the rotated spin)
+  int nvec;     // number of vectors (strings of the other spin)
+  int lgKV;     // log2 of vectors per slab
+  int chunk;    // vector elements held by one CTA of the cluster
+  const uint32_t* pairs;
+  int npp;
+  const uint32_t* masks_this;
+  const uint32_t* masks_other;
+  int norb;
+  int nchunk;  // 8-bit chunks of a string mask
+  const void* ea_this;
+  const void* ea_other;
+  int has_x;  // cross angles X[p_alpha][q_beta] are passed separately
+  // reverse mode (dual state: st[0] = psi, st[1] = cotangent g)
+  const void* ea2_this;   // second phase (applied after the reductions)
+  const void* ea2_other;
+  const uint32_t* xpairs;  // E_pq pair lists of the rotated spin
+  const uint32_t* xsign;
+  const int* xcount;
+  int nx;
+  double* T;  // [norb][norb] complex accumulator: += <g| E_pq |psi>
+  void* W;    // [d_a][d_b] real: Im(conj(g) psi), or null
+};
+
+// exp(i x) for an FP64 angle: reduced to [-pi, pi] in FP64, then evaluated
+// in the precision of the state.
+template <typename R>
+__device__ __forceinline__ cx_t<R> expi(double x);
+template <>
+__device__ __forceinline__ cx_t<float> expi<float>(double x) {
+  double r = x - 6.283185307179586 * rint(x * 0.15915494309189535);
+  float s, c;
+  sincosf((float)r, &s, &c);
+  return mk<float>(c, s);
+}
+template <>
+__device__ __forceinline__ cx_t<double> expi<double>(double x) {
+  double r = x - 6.283185307179586 * rint(x * 0.15915494309189535);
+  double s, c;
+  sincos(r, &s, &c);
+  return mk<double>(c, s);
+}
+
+// Cross-term tables for the slab vectors o = v0 .. v0+nv-1 (other-spin
+// strings): w[kv][x] = sum_{y in I_o} X[y][x] (this = beta) or X[x][y]
+// (this = alpha), and tab[kv][c][v] = exp(i sum_{bits b of v} w[kv][8c + b]).
+// Ends with a block barrier.
+template <typename R>
+__device__ void build_cross_tables(const SweepGeom& g, const Mat& X, int v0, int nv,
+                                   double* w, cx_t<R>* tab, int tid, int nthr) {
+  for (int idx = tid; idx < nv * g.norb; idx += nthr) {
+    int kv = idx / g.norb, x = idx - kv * g.norb;
+    double s = 0;
+    uint32_t m = g.masks_other[v0 + kv];
+    while (m) {
+      int y = __ffs(m) - 1;
+      m &= m - 1;
+      s += g.dir == 1 ? X.v[y * g.norb + x] : X.v[x * g.norb + y];
+    }
+    w[kv * kMaxOrb + x] = s;
+  }
+  __syncthreads();
+  const int per = g.nchunk * 256;
+  for (int idx = tid; idx < nv * per; idx += nthr) {
+    int kv = idx / per, e = idx - kv * per;
+    int c = e >> 8, v = e & 255;
+    double s = 0;
+    while (v) {
+      int b = __ffs(v) - 1;
+      v &= v - 1;
+      int x = 8 * c + b;
+      if (x < g.norb) s += w[kv * kMaxOrb + x];
+    }
+    tab[idx] = expi<R>(s);
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
+  if (!p) return mk<R>(1, 0);
+  return reinterpret_cast<const cx_t<R>*>(p)[i];
+}
+
+template <typename R, int CS, int NST, bool VJP>
+__global__ void __launch_bounds__(kThreads)
+    k_sweep(const SweepGeom g, const __grid_constant__ GProg<R> prog,
+            const __grid_constant__ Mat X) {
+  static_assert(!VJP || NST == 2, "reverse mode carries two states");
+  using C = cx_t<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int KV = 1 << g.lgKV;
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int slab = blockIdx.x / CS;
+  const int v0 = slab * KV;
+  const int kv_eff = min(KV, g.nvec - v0);
+  const int e0 = rank * g.chunk;
+  const int nel = max(0, min(g.d - e0, g.chunk));
+  const int tid = threadIdx.x;
+  const size_t st_stride = (size_t)g.chunk * KV;  // elements per state
+  C* tab = sm + NST * st_stride;                  // cross tables, KV sets
+  double* w = reinterpret_cast<double*>(tab + (g.has_x ? ((size_t)g.nchunk * 256 << g.lgKV) : 0));
+
+  C* base[CS];
+  if constexpr (CS > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    for (int r = 0; r < CS; ++r) base[r] = cl.map_shared_rank(sm, r);
+  } else {
+    base[0] = sm;
+  }
+
+  // ---- load this CTA's part of the slab
+  for (int s = 0; s < NST; ++s) {
+    const C* gs = reinterpret_cast<const C*>(g.st[s]);
+    C* ss = sm + s * st_stride;
+    if (g.dir == 1) {
+      for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
+        int kv = idx / nel, el = idx - kv * nel;
+        ss[(size_t)el * KV + kv] = gs[(int64_t)(v0 + kv) * g.d_b + e0 + el];
+      }
+    } else {
+      for (int idx = tid; idx < (nel << g.lgKV); idx += kThreads) {
+        int el = idx >> g.lgKV, kv = idx & (KV - 1);
+        if (kv < kv_eff) ss[(size_t)el * KV + kv] = gs[(int64_t)(e0 + el) * g.d_b + v0 + kv];
+      }
+    }
+  }
+  if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+
+  // ---- Givens rotations, in program order
+  const int items = g.npp << g.lgKV;
+  const int per = (items + CS - 1) / CS;
+  const int lo = rank * per, hi = min(items, lo + per);
+  for (int k = 0; k < prog.m; ++k) {
+    const uint32_t* list = g.pairs + (int64_t)prog.p[k] * g.npp;
+    const R c = prog.c[k], sr = prog.sr[k], si = prog.si[k];
+    for (int it = lo + tid; it < hi; it += kThreads) {
+      int t = it >> g.lgKV, kv = it & (KV - 1);
+      if (kv >= kv_eff) continue;
+      uint32_t pr = __ldg(list + t);
+      int src = pr & 0xFFFF, dst = pr >> 16;
+      int os = 0, od = 0;
+      if constexpr (CS > 1) {
+#pragma unroll
+        for (int r = 1; r < CS; ++r) {
+          os += src >= r * g.chunk;
+          od += dst >= r * g.chunk;
+        }
+      }
+      size_t ls = (size_t)(src - os * g.chunk) * KV + kv;
+      size_t ld = (size_t)(dst - od * g.chunk) * KV + kv;
+#pragma unroll
+      for (int s = 0; s < NST; ++s) {
+        C* ps = base[os] + s * st_stride + ls;
+        C* pd = base[od] + s * st_stride + ld;
+        C x = *ps, y = *pd;
+        givens2<R>(x, y, c, sr, si);
+        *ps = x;
+        *pd = y;
+      }
+    }
+    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+  }
+
+  const int tper = g.nchunk * 256;
+  if constexpr (!VJP) {
+    // ---- epilogue: phases, store
+    if (g.has_x) build_cross_tables<R>(g, X, v0, kv_eff, w, tab, tid, kThreads);
+    const int tot = g.dir == 1 ? kv_eff * nel : (nel << g.lgKV);
+    for (int idx = tid; idx < tot; idx += kThreads) {
+      int kv, el;
+      if (g.dir == 1) {
+        kv = idx / nel;
+        el = idx - kv * nel;
+      } else {
+        el = idx >> g.lgKV;
+        kv = idx & (KV - 1);
+        if (kv >= kv_eff) continue;
+      }
+      const int o = v0 + kv, e = e0 + el;
+      C f = cmul<R>(ld_ea<R>(g.ea_other, o), ld_ea<R>(g.ea_this, e));
+      if (g.has_x) {
+        uint32_t m = __ldg(g.masks_this + e);
+        const C* tk = tab + kv * tper;
+        for (int c = 0; c < g.nchunk; ++c) f = cmul<R>(f, tk[c * 256 + ((m >> (8 * c)) & 255)]);
+      }
+#pragma unroll
+      for (int s = 0; s < NST; ++s) {
+        C v = cmul<R>(f, sm[s * st_stride + (size_t)el * KV + kv]);
+        C* gs = reinterpret_cast<C*>(g.st[s]);
+        if (g.dir == 1)
+          gs[(int64_t)o * g.d_b + e] = v;
+        else
+          gs[(int64_t)e * g.d_b + o] = v;
+      }
+    }
+  } else {
+    // ---- reverse-mode epilogue
+    // (a) the diagonal layer of the (inverse) rotation, in shared memory
+    for (int idx = tid; idx < (nel << g.lgKV); idx += kThreads) {
+      int el = idx >> g.lgKV, kv = idx & (KV - 1);
+      if (kv >= kv_eff) continue;
+      C f = cmul<R>(ld_ea<R>(g.ea_other, v0 + kv), ld_ea<R>(g.ea_this, e0 + el));
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        C* q = sm + s * st_stride + (size_t)el * KV + kv;
+        *q = cmul<R>(f, *q);
+      }
+    }
+    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    // (b) T[p][q] += sum over the slab of sign * conj(g[dst]) * psi[src] for
+    //     every pair (src, dst = src^{q->p}) of the E_pq list of this spin
+    if (g.T) {
+      const int lane = tid & 31;
+      const int nw = (g.nx + 31) / 32;
+      const int gw = rank * (kThreads / 32) + (tid >> 5);
+      const int nlist = g.norb * g.norb;
+      for (int L = gw; L < nlist; L += CS * (kThreads / 32)) {
+        const int cnt = g.xcount[L];
+        const uint32_t* lp = g.xpairs + (int64_t)L * g.nx;
+        const uint32_t* ls = g.xsign + (int64_t)L * nw;
+        R ar = 0, ai = 0;
+        for (int t = lane; t < cnt; t += 32) {
+          uint32_t pr = __ldg(lp + t);
+          uint32_t sb = (__ldg(ls + (t >> 5)) >> (t & 31)) & 1u;
+          int src = pr & 0xFFFF, dst = pr >> 16;
+          int os = 0, od = 0;
+          if constexpr (CS > 1) {
+#pragma unroll
+            for (int r = 1; r < CS; ++r) {
+              os += src >= r * g.chunk;
+              od += dst >= r * g.chunk;
+            }
+          }
+          const C* ps = base[os] + (size_t)(src - os * g.chunk) * KV;
+          const C* pg = base[od] + st_stride + (size_t)(dst - od * g.chunk) * KV;
+          R br = 0, bi = 0;
+          for (int kv = 0; kv < kv_eff; ++kv) {
+            C a = ps[kv], b = pg[kv];
+            br = fma(b.x, a.x, fma(b.y, a.y, br));
+            bi = fma(b.x, a.y, fma(-b.y, a.x, bi));
+          }
+          if (sb) { br = -br; bi = -bi; }
+          ar += br;
+          ai += bi;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          ar += __shfl_xor_sync(0xFFFFFFFFu, ar, off);
+          ai += __shfl_xor_sync(0xFFFFFFFFu, ai, off);
+        }
+        if (lane == 0) {
+          atomicAdd(g.T + 2 * L, (double)ar);
+          atomicAdd(g.T + 2 * L + 1, (double)ai);
+        }
+      }
+    }
+    // (c) W = Im(conj(g) psi) (invariant under the diagonal gate that
+    //     follows), then the second phase, then store both states
+    if (g.has_x) build_cross_tables<R>(g, X, v0, kv_eff, w, tab, tid, kThreads);
+    const int tot = g.dir == 1 ? kv_eff * nel : (nel << g.lgKV);
+    for (int idx = tid; idx < tot; idx += kThreads) {
+      int kv, el;
+      if (g.dir == 1) {
+        kv = idx / nel;
+        el = idx - kv * nel;
+      } else {
+        el = idx >> g.lgKV;
+        kv = idx & (KV - 1);
+        if (kv >= kv_eff) continue;
+      }
+      const int o = v0 + kv, e = e0 + el;
+      const int64_t gi = g.dir == 1 ? (int64_t)o * g.d_b + e : (int64_t)e * g.d_b + o;
+      C ps = sm[(size_t)el * KV + kv];
+      C pg = sm[st_stride + (size_t)el * KV + kv];
+      if (g.W) reinterpret_cast<R*>(g.W)[gi] = pg.x * ps.y - pg.y * ps.x;
+      C f = cmul<R>(ld_ea<R>(g.ea2_other, o), ld_ea<R>(g.ea2_this, e));
+      if (g.has_x) {
+        uint32_t m = __ldg(g.masks_this + e);
+        const C* tk = tab + kv * tper;
+        for (int c = 0; c < g.nchunk; ++c) f = cmul<R>(f, tk[c * 256 + ((m >> (8 * c)) & 255)]);
+      }
+      reinterpret_cast<C*>(g.st[0])[gi] = cmul<R>(f, ps);
+      reinterpret_cast<C*>(g.st[1])[gi] = cmul<R>(f, pg);
+    }
+    // remote CTAs may still read this CTA's shared memory in (b)
+    if constexpr (CS > 1) cg::this_cluster().sync();
+  }
+}
+
+template <typename R>
+static GProg<R> make_prog(const RotProgram& rp) {
+  GProg<R> p;
+  p.m = (int)rp.g.size();
+  for (int k = 0; k < p.m; ++k) {
+    p.p[k] = (int8_t)rp.g[k].p;
+    p.c[k] = (R)rp.g[k].c;
+    p.sr[k] = (R)rp.g[k].s.real();
+    p.si[k] = (R)rp.g[k].s.imag();
+  }
+  return p;
+}
+
+template <typename R, int CS, int NST, bool VJP>
+static void launch_sweep_t(const SweepGeom& g, const GProg<R>& prog, const Mat& X,
+                           int nslabs, size_t smem, cudaStream_t st) {
+  auto kern = k_sweep<R, CS, NST, VJP>;
+  FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nslabs * CS));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CS > 1 ? 1 : 0;
+  FS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, prog, X));
+}
+
+template <typename R, int NST, bool VJP>
+static void dispatch_cs(int CS, const SweepGeom& g, const GProg<R>& prog, const Mat& X,
+                        int nslabs, size_t smem, cudaStream_t st) {
+  switch (CS) {
+    case 1: launch_sweep_t<R, 1, NST, VJP>(g, prog, X, nslabs, smem, st); break;
+    case 2: launch_sweep_t<R, 2, NST, VJP>(g, prog, X, nslabs, smem, st); break;
+    case 4: launch_sweep_t<R, 4, NST, VJP>(g, prog, X, nslabs, smem, st); break;
+    case 8: launch_sweep_t<R, 8, NST, VJP>(g, prog, X, nslabs, smem, st); break;
+    default: FS_REQUIRE(false, FS_ERR_UNSUPPORTED, "cluster size out of range");
+  }
+}
+
+void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0,
+                  void* st1, int nst, int dtype, const RotProgram& rp,
+                  const PhaseDev& ph, cudaStream_t st, const RevArgs* rev) {
+  FS_REQUIRE((nst == 2) == (rev != nullptr), FS_ERR_ARG, "reverse mode needs two states");
+  const Space* sthis = dir == 0 ? sa : sb;
+  const Space* sother = dir == 0 ? sb : sa;
+  FS_REQUIRE(sthis->dim <= kMaxSweepDim, FS_ERR_UNSUPPORTED,
+             "string dimension above 65535 is not supported by the sweep kernels");
+  FS_REQUIRE((int)rp.g.size() <= kMaxGivens, FS_ERR_ARG, "too many Givens rotations");
+  SweepGeom g{};
+  g.st[0] = st0;
+  g.st[1] = st1;
+  g.d_b = sb->dim;
+  g.dir = dir;
+  g.d = (int)sthis->dim;
+  g.nvec = (int)sother->dim;
+  g.pairs = sthis->pairs;
+  g.npp = sthis->npp;
+  g.masks_this = sthis->masks;
+  g.masks_other = sother->masks;
+  g.norb = sthis->norb;
+  g.nchunk = (sthis->norb + 7) / 8;
+  g.ea_this = dir == 0 ? ph.ea_a : ph.ea_b;
+  g.ea_other = dir == 0 ? ph.ea_b : ph.ea_a;
+  g.has_x = ph.has_x;
+  if (rev) {
+    g.ea2_this = dir == 0 ? rev->ea2_a : rev->ea2_b;
+    g.ea2_other = dir == 0 ? rev->ea2_b : rev->ea2_a;
+    g.xpairs = sthis->xpairs;
+    g.xsign = sthis->xsign;
+    g.xcount = sthis->xcount;
+    g.nx = sthis->nx;
+    g.T = sthis->nx > 0 ? rev->T : nullptr;
+    g.W = rev->W;
+  }
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  const size_t maxsm = (size_t)ctx->prop.sharedMemPerBlockOptin;
+  const size_t tab_per_kv = ph.has_x ? g.nchunk * 256 * csz : 0;
+  const size_t fixed = ph.has_x ? kMaxOrb * sizeof(double) : 0;
+  auto smem_for = [&](int CS, int KV) {
+    size_t chunk = (g.d + CS - 1) / CS;
+    return (size_t)KV * (chunk * csz * nst + tab_per_kv + fixed);
+  };
+  int CS = 1;
+  while (CS <= 8 && smem_for(CS, 1) > maxsm) CS *= 2;
+  FS_REQUIRE(CS <= 8, FS_ERR_UNSUPPORTED, "state vector too large for a cluster of 8");
+  // vectors per slab: fit shared memory, keep >= 2 slabs per SM when possible
+  int want = std::max(1, g.nvec / (2 * ctx->prop.multiProcessorCount));
+  int lg = 0;
+  while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(CS, 2 << lg) <= maxsm) ++lg;
+  g.lgKV = lg;
+  g.chunk = (g.d + CS - 1) / CS;
+  const int KV = 1 << lg;
+  const int nslabs = (g.nvec + KV - 1) / KV;
+  const size_t smem = std::max<size_t>(smem_for(CS, KV), 16);
+  if (dtype == FS_C64) {
+    auto prog = make_prog<float>(rp);
+    if (nst == 1) dispatch_cs<float, 1, false>(CS, g, prog, ph.X, nslabs, smem, st);
+    else dispatch_cs<float, 2, true>(CS, g, prog, ph.X, nslabs, smem, st);
+  } else {
+    auto prog = make_prog<double>(rp);
+    if (nst == 1) dispatch_cs<double, 1, false>(CS, g, prog, ph.X, nslabs, smem, st);
+    else dispatch_cs<double, 2, true>(CS, g, prog, ph.X, nslabs, smem, st);
+  }
+}
+
+// ------------------------------------------------------------------ phase
+// One streaming pass: psi[i][j] *= ea_a[i] ea_b[j] exp(i sum X[p][q]) with
+// the cross tables built per row from the alpha string.
+template <typename R>
+__global__ void __launch_bounds__(256)
+    k_phase(cx_t<R>* vec, int64_t da, int64_t db, const uint32_t* ma,
+            const uint32_t* mb, int norb, int nchunk, const void* ea_a,
+            const void* ea_b, int has_x, const __grid_constant__ Mat X) {
+  using C = cx_t<R>;
+  __shared__ double w[kMaxOrb];
+  __shared__ C tab[4 * 256];
+  SweepGeom g{};
+  g.dir = 1;
+  g.norb = norb;
+  g.nchunk = nchunk;
+  g.has_x = has_x;
+  g.masks_other = ma;
+  for (int64_t i = blockIdx.x; i < da; i += gridDim.x) {
+    C fa = ld_ea<R>(ea_a, i);
+    if (has_x) {
+      __syncthreads();
+      build_cross_tables<R>(g, X, (int)i, 1, w, tab, threadIdx.x, blockDim.x);
+    }
+    C* row = vec + i * db;
+    for (int64_t j = threadIdx.x; j < db; j += blockDim.x) {
+      C f = cmul<R>(fa, ld_ea<R>(ea_b, j));
+      if (has_x) {
+        uint32_t m = __ldg(mb + j);
+        for (int c = 0; c < nchunk; ++c) f = cmul<R>(f, tab[c * 256 + ((m >> (8 * c)) & 255)]);
+      }
+      row[j] = cmul<R>(f, row[j]);
+    }
+  }
+}
+
+void launch_phase(const Space* sa, const Space* sb, void* vec, int dtype,
+                  const PhaseDev& ph, cudaStream_t st) {
+  int nchunk = (sa->norb + 7) / 8;
+  unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 4096);
+  if (dtype == FS_C64)
+    k_phase<float><<<grid, 256, 0, st>>>((float2*)vec, sa->dim, sb->dim, sa->masks,
+                                         sb->masks, sa->norb, nchunk, ph.ea_a,
+                                         ph.ea_b, ph.has_x, ph.X);
+  else
+    k_phase<double><<<grid, 256, 0, st>>>((double2*)vec, sa->dim, sb->dim, sa->masks,
+                                          sb->masks, sa->norb, nchunk, ph.ea_a,
+                                          ph.ea_b, ph.has_x, ph.X);
+  FS_CUDA(cudaGetLastError());
+}
+
+// Per-string factors (FP64 arithmetic, stored in the state precision).
+template <typename R>
+__global__ void k_string_phase(cx_t<R>* out, const uint32_t* masks, int64_t dim,
+                               int norb, const __grid_constant__ StrPhase f) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  uint32_t m = masks[e];
+  double re = 1, im = 0, ang = 0;
+  for (int p = 0; p < norb; ++p) {
+    if (!((m >> p) & 1u)) continue;
+    if (f.use_d) {
+      double dr = f.d[2 * p], di = f.d[2 * p + 1];
+      double nr = re * dr - im * di;
+      im = re * di + im * dr;
+      re = nr;
+    }
+    if (f.use_lam) ang -= f.t * f.lam[p];
+    if (f.use_j)
+      for (int q = 0; q < norb; ++q)
+        if ((m >> q) & 1u) ang -= 0.5 * f.t * f.J.v[p * norb + q];
+  }
+  double r = ang - 6.283185307179586 * rint(ang * 0.15915494309189535);
+  double s, c;
+  sincos(r, &s, &c);
+  out[e] = mk<R>((R)(re * c - im * s), (R)(re * s + im * c));
+}
+
+void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& f,
+                         cudaStream_t st) {
+  unsigned grid = (unsigned)((sp->dim + 127) / 128);
+  if (dtype == FS_C64)
+    k_string_phase<float><<<grid, 128, 0, st>>>((float2*)out, sp->masks, sp->dim,
+                                                 sp->norb, f);
+  else
+    k_string_phase<double><<<grid, 128, 0, st>>>((double2*)out, sp->masks, sp->dim,
+                                                  sp->norb, f);
+  FS_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------- Hartree-Fock closed form
+// v[e] = det(R[I_e, 0..n-1]) by Gaussian elimination with partial pivoting,
+// FP64.
+__global__ void k_slater_minors(const uint32_t* masks, int64_t dim, int norb, int n,
+                                const __grid_constant__ CMat R, double2* v) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  double2 a[kMaxOrb * kMaxOrb];
+  uint32_t m = masks[e];
+  int r = 0;
+  for (int p = 0; p < norb; ++p)
+    if ((m >> p) & 1u) {
+      for (int c = 0; c < n; ++c)
+        a[r * n + c] = make_double2(R.v[2 * (p * norb + c)], R.v[2 * (p * norb + c) + 1]);
+      ++r;
+    }
+  double dr = 1, di = 0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = hypot(a[k * n + k].x, a[k * n + k].y);
+    for (int i = k + 1; i < n; ++i) {
+      double h = hypot(a[i * n + k].x, a[i * n + k].y);
+      if (h > best) { best = h; piv = i; }
+    }
+    if (best == 0) { dr = 0; di = 0; break; }
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) { double2 t = a[k * n + c]; a[k * n + c] = a[piv * n + c]; a[piv * n + c] = t; }
+      dr = -dr; di = -di;
+    }
+    double2 pk = a[k * n + k];
+    double nr = dr * pk.x - di * pk.y;
+    di = dr * pk.y + di * pk.x;
+    dr = nr;
+    double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
+    for (int i = k + 1; i < n; ++i) {
+      double2 x = a[i * n + k];
+      double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
+      for (int c = k + 1; c < n; ++c) {
+        double2 y = a[k * n + c];
+        a[i * n + c].x -= fr * y.x - fi * y.y;
+        a[i * n + c].y -= fr * y.y + fi * y.x;
+      }
+    }
+  }
+  v[e] = make_double2(dr, di);
+}
+
+template <typename R>
+__global__ void k_outer(cx_t<R>* vec, const double2* va, const double2* vb, int64_t da,
+                        int64_t db) {
+  int64_t n = da * db;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = k / db, j = k - i * db;
+    double2 a = va[i], b = vb[j];
+    vec[k] = mk<R>((R)(a.x * b.x - a.y * b.y), (R)(a.x * b.y + a.y * b.x));
+  }
+}
+
+void launch_slater(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dtype,
+                   const CMat& R, cudaStream_t st) {
+  double2* va = (double2*)scratch(ctx, "slater_a", sa->dim * 16);
+  double2* vb = (double2*)scratch(ctx, "slater_b", sb->dim * 16);
+  k_slater_minors<<<(unsigned)((sa->dim + 63) / 64), 64, 0, st>>>(
+      sa->masks, sa->dim, sa->norb, sa->nocc, R, va);
+  FS_CUDA(cudaGetLastError());
+  k_slater_minors<<<(unsigned)((sb->dim + 63) / 64), 64, 0, st>>>(
+      sb->masks, sb->dim, sb->norb, sb->nocc, R, vb);
+  FS_CUDA(cudaGetLastError());
+  int64_t n = sa->dim * sb->dim;
+  unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  if (dtype == FS_C64)
+    k_outer<float><<<grid, 256, 0, st>>>((float2*)vec, va, vb, sa->dim, sb->dim);
+  else
+    k_outer<double><<<grid, 256, 0, st>>>((double2*)vec, va, vb, sa->dim, sb->dim);
+  FS_CUDA(cudaGetLastError());
+}
+
+}  // namespace fs

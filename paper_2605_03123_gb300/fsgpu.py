@@ -1,0 +1,264 @@
+"""Thin Python binding of libfsgpu.so (include/fsgpu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  There is
+no CPU fallback: if the library is missing or no GPU is present, calls raise.
+
+State tensors are complex64 or complex128 CUDA tensors of shape
+(dim_a, dim_b), contiguous, in the address convention of the C header.
+Functional calls return a new tensor (the paper's style, §4.1); the `*_`
+variants update in place.
+"""
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import lib_path
+
+FS_C64, FS_C128 = 0, 1
+FS_ROT_AUTO, FS_ROT_GIVENS, FS_ROT_MINORS = 0, 1, 2
+
+STATUS = {0: "FS_OK", -1: "FS_ERR_ARG", -2: "FS_ERR_NOT_UNITARY", -3: "FS_ERR_NOMEM",
+          -4: "FS_ERR_CUDA", -5: "FS_ERR_TIMEOUT", -6: "FS_ERR_BOUNDS",
+          -7: "FS_ERR_UNSUPPORTED"}
+
+
+class FsError(RuntimeError):
+    def __init__(self, func, code, msg):
+        super().__init__("%s failed: %s (%d): %s" % (func, STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class LUCJ(ctypes.Structure):
+    _fields_ = [("norb", ctypes.c_int), ("n_alpha", ctypes.c_int), ("n_beta", ctypes.c_int),
+                ("n_reps", ctypes.c_int), ("K", ctypes.c_void_p), ("J_aa", ctypes.c_void_p),
+                ("J_ab", ctypes.c_void_p), ("from_hf", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "fs_create": [ctypes.POINTER(_P), _I],
+    "fs_destroy": [_P],
+    "fs_last_error": [],
+    "fs_sync_status": [_P, _P],
+    "fs_set_rotation_path": [_P, _I],
+    "fs_string_table": [_P, _I, _I, _P, _I64],
+    "fs_excitation_table": [_P, _I, _I, _P, _I64],
+    "fs_apply_orbital_rotation": [_P, _P, _I, _P, _P, _I, _I, _I, _P],
+    "fs_apply_num_op_sum_evolution": [_P, _P, _I, _P, _P, _D, _I, _I, _I, _P],
+    "fs_apply_diag_coulomb_evolution": [_P, _P, _I, _P, _P, _P, _D, _I, _I, _I, _P],
+    "fs_lucj_forward": [_P, ctypes.POINTER(LUCJ), _P, _I, _P],
+    "fs_lucj_vjp": [_P, ctypes.POINTER(LUCJ), _P, _P, _I, _P, _P, _P, _P],
+}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path=None):
+    """Load libfsgpu.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise FsError("load_library", -7, "%s is missing; build it with "
+                          "paper_2605_03123_gb300.build.build()" % p)
+        lib = ctypes.CDLL(p)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "fs_last_error" else ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise FsError(name, rc, load_library().fs_last_error().decode())
+
+
+class Context:
+    """A library context on one CUDA device (tables and scratch live here)."""
+
+    def __init__(self, device=0):
+        lib = load_library()
+        h = _P()
+        _check("fs_create", lib.fs_create(ctypes.byref(h), int(device)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _check("fs_destroy", load_library().fs_destroy(self.handle))
+            self.handle = None
+
+    def set_rotation_path(self, path):
+        _check("fs_set_rotation_path", load_library().fs_set_rotation_path(self.handle, int(path)))
+
+    def sync_status(self, stream=None):
+        return load_library().fs_sync_status(self.handle, _stream_ptr(stream))
+
+
+_contexts = {}
+
+
+def context(device=None):
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return FS_C64
+    if t.dtype == torch.complex128:
+        return FS_C128
+    raise TypeError("state must be complex64 or complex128, got %s" % t.dtype)
+
+
+def _check_state(vec, norb, nelec):
+    from math import comb
+    if not vec.is_cuda:
+        raise ValueError("state must be a CUDA tensor (there is no CPU path)")
+    shape = (comb(norb, nelec[0]), comb(norb, nelec[1]))
+    if tuple(vec.shape) != shape:
+        raise ValueError("state shape %s, expected %s" % (tuple(vec.shape), shape))
+    if not vec.is_contiguous():
+        raise ValueError("state must be contiguous")
+
+
+def _f64(a, shape=None, complex_=False):
+    a = np.ascontiguousarray(a, dtype=np.complex128 if complex_ else np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_P) if a is not None else None
+
+
+# ----------------------------------------------------------------- tables
+def string_table(norb, nocc, ctx=None):
+    from math import comb
+    ctx = ctx or context()
+    out = np.zeros(comb(norb, nocc), np.uint32)
+    _check("fs_string_table", load_library().fs_string_table(ctx.handle, norb, nocc,
+                                                             _ptr(out), out.size))
+    return out
+
+
+def excitation_table(norb, nocc, ctx=None):
+    from math import comb
+    ctx = ctx or context()
+    d = comb(norb, nocc)
+    out = np.zeros(d * norb * norb, np.uint32)
+    _check("fs_excitation_table", load_library().fs_excitation_table(
+        ctx.handle, norb, nocc, _ptr(out), out.size))
+    return out.reshape(d, norb, norb)
+
+
+# ------------------------------------------------------------------ gates
+def apply_orbital_rotation_(vec, U, norb, nelec, U_b=None, ctx=None):
+    _check_state(vec, norb, nelec)
+    ctx = ctx or context(vec.device.index)
+    Ua = _f64(U, (norb, norb), True)
+    Ub = None if U_b is None else _f64(U_b, (norb, norb), True)
+    _check("fs_apply_orbital_rotation", load_library().fs_apply_orbital_rotation(
+        ctx.handle, _P(vec.data_ptr()), _dtype_code(vec), _ptr(Ua), _ptr(Ub), norb,
+        nelec[0], nelec[1], _stream_ptr()))
+    return vec
+
+
+def apply_orbital_rotation(vec, U, norb, nelec, U_b=None, ctx=None):
+    return apply_orbital_rotation_(vec.clone(), U, norb, nelec, U_b, ctx)
+
+
+def apply_num_op_sum_evolution_(vec, lam, t, norb, nelec, lam_b=None, ctx=None):
+    _check_state(vec, norb, nelec)
+    ctx = ctx or context(vec.device.index)
+    la = _f64(lam, (norb,))
+    lb = None if lam_b is None else _f64(lam_b, (norb,))
+    _check("fs_apply_num_op_sum_evolution", load_library().fs_apply_num_op_sum_evolution(
+        ctx.handle, _P(vec.data_ptr()), _dtype_code(vec), _ptr(la), _ptr(lb), float(t),
+        norb, nelec[0], nelec[1], _stream_ptr()))
+    return vec
+
+
+def apply_num_op_sum_evolution(vec, lam, t, norb, nelec, lam_b=None, ctx=None):
+    return apply_num_op_sum_evolution_(vec.clone(), lam, t, norb, nelec, lam_b, ctx)
+
+
+def apply_diag_coulomb_evolution_(vec, J_aa, J_ab, t, norb, nelec, J_bb=None, ctx=None):
+    _check_state(vec, norb, nelec)
+    ctx = ctx or context(vec.device.index)
+    a = _f64(J_aa, (norb, norb))
+    b = _f64(J_ab, (norb, norb))
+    c = None if J_bb is None else _f64(J_bb, (norb, norb))
+    _check("fs_apply_diag_coulomb_evolution", load_library().fs_apply_diag_coulomb_evolution(
+        ctx.handle, _P(vec.data_ptr()), _dtype_code(vec), _ptr(a), _ptr(b), _ptr(c), float(t),
+        norb, nelec[0], nelec[1], _stream_ptr()))
+    return vec
+
+
+def apply_diag_coulomb_evolution(vec, J_aa, J_ab, t, norb, nelec, J_bb=None, ctx=None):
+    return apply_diag_coulomb_evolution_(vec.clone(), J_aa, J_ab, t, norb, nelec, J_bb, ctx)
+
+
+# ------------------------------------------------------------------- LUCJ
+def _lucj_struct(K, J_aa, J_ab, norb, nelec, from_hf):
+    K = _f64(K, None, True)
+    J_aa = _f64(J_aa)
+    J_ab = _f64(J_ab)
+    n_reps = K.shape[0]
+    if K.shape != (n_reps, norb, norb) or J_aa.shape != K.shape or J_ab.shape != K.shape:
+        raise ValueError("K, J_aa, J_ab must have shape (n_reps, norb, norb)")
+    op = LUCJ(norb, nelec[0], nelec[1], n_reps, K.ctypes.data, J_aa.ctypes.data,
+              J_ab.ctypes.data, int(bool(from_hf)))
+    return op, (K, J_aa, J_ab)
+
+
+def lucj_forward_(vec, K, J_aa, J_ab, norb, nelec, from_hf=False, ctx=None):
+    _check_state(vec, norb, nelec)
+    ctx = ctx or context(vec.device.index)
+    op, keep = _lucj_struct(K, J_aa, J_ab, norb, nelec, from_hf)
+    _check("fs_lucj_forward", load_library().fs_lucj_forward(
+        ctx.handle, ctypes.byref(op), _P(vec.data_ptr()), _dtype_code(vec), _stream_ptr()))
+    return vec
+
+
+def lucj_vjp_(vec, cot, K, J_aa, J_ab, norb, nelec, from_hf=False, ctx=None):
+    """In place: vec (forward output) -> recomputed input, cot -> dL/dpsi_in.
+    Returns (dK, dJ_aa, dJ_ab) as NumPy arrays."""
+    _check_state(vec, norb, nelec)
+    _check_state(cot, norb, nelec)
+    if cot.dtype != vec.dtype:
+        raise TypeError("state and cotangent must have the same dtype")
+    ctx = ctx or context(vec.device.index)
+    op, keep = _lucj_struct(K, J_aa, J_ab, norb, nelec, from_hf)
+    n_reps = op.n_reps
+    dK = np.zeros((n_reps, norb, norb), np.complex128)
+    dJa = np.zeros((n_reps, norb, norb))
+    dJb = np.zeros((n_reps, norb, norb))
+    _check("fs_lucj_vjp", load_library().fs_lucj_vjp(
+        ctx.handle, ctypes.byref(op), _P(vec.data_ptr()), _P(cot.data_ptr()),
+        _dtype_code(vec), _ptr(dK), _ptr(dJa), _ptr(dJb), _stream_ptr()))
+    return dK, dJa, dJb
