@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark: LUCJ forward + VJP layers/s at norb = 16, nelec = (8, 8).
+
+Workload (one step = one pass of the whole path): the 10-layer LUCJ circuit
+of the N=16 (8,8) workload (Haar-random orbital rotations, diagonal-Coulomb
+couplings ~ N(0, 0.5) at t = 0.3, random normalised initial state,
+1.66e8 amplitudes), forward pass then VJP by uncomputation, complex64 state
+and FP32 arithmetic.  value = 10 layers / step time.  The same workload runs
+once in complex128 for the c64-vs-c128 figure.
+
+Prints one JSON line on rank 0.  `--impl reference` times the oracle (plain
+CPU NumPy) on a bounded sample of the same workload instead.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NORB, NELEC, NLAYERS = 16, (8, 8), 10
+WORKLOAD = "lucj_fwd_vjp_norb16_nelec8_8_10layers"
+METRIC = "LUCJ fwd+VJP layers/s at norb=16 (8,8)"
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_03123_gb300", "csrc", "fs_sweep.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(parts) >= 4 and parts[0] == kernel and parts[3] == h:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload
+def workload(args=None):
+    from paper_2605_03123_gb300 import inputs
+    if args is not None and args.norb:
+        return inputs.lucj_layers(args.norb, (args.nalpha, args.nbeta), args.layers, 0.5, 0.3,
+                                  2000 + 99)
+    return inputs.plain_at_scale()
+
+
+def algorithmic_bytes(kernel, S, n_layers):
+    """Bytes the method itself must move per launch of each kernel kind:
+    a sweep reads and writes its state(s) once; the reverse alpha sweep also
+    writes W (real, half a state) for the layers that have a gate to undo."""
+    if kernel.startswith("sweep_vjp_alpha"):
+        return 4 * S + 0.5 * S * n_layers / (n_layers + 1)
+    if kernel.startswith("sweep_vjp"):
+        return 4 * S
+    if kernel.startswith("sweep"):
+        return 2 * S
+    if kernel.startswith("phase"):
+        return 2 * S
+    return None
+
+
+def run_gpu(args):
+    import torch
+    from paper_2605_03123_gb300 import fsgpu
+
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fsgpu.load_library()
+    ctx = fsgpu.context(local)
+    global NORB, NELEC, NLAYERS, WORKLOAD
+    w = workload(args)
+    if args.norb:
+        NORB, NELEC, NLAYERS = args.norb, (args.nalpha, args.nbeta), args.layers
+        WORKLOAD = "lucj_fwd_vjp_norb%d_nelec%d_%d_%dlayers" % (NORB, NELEC[0], NELEC[1], NLAYERS)
+    K, Jaa, Jab = w["K"], w["J_aa"], w["J_ab"]
+    da, db = math.comb(NORB, NELEC[0]), math.comb(NORB, NELEC[1])
+    S = 8 * da * db
+    vec0 = torch.from_numpy(w["vec"].astype(np.complex64)).cuda()
+    cot0 = torch.from_numpy(w["cot"].astype(np.complex64)).cuda()
+    vec = vec0.clone()
+    cot = torch.empty_like(cot0)
+
+    def step():
+        cot.copy_(cot0)
+        fsgpu.lucj_forward_(vec, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+        return fsgpu.lucj_vjp_(vec, cot, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ctx.profile_start()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile_stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * NLAYERS * args.steps / (ms / 1e3)
+    launches = sum(v[2] for v in prof.values())
+
+    # parity at full size, properties: recovered input and dL/dpsi_in identities
+    rec_err = float((vec - vec0).abs().max().item())
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hv = torch.from_numpy(w["vec"].astype(np.complex64)).pin_memory()
+        hc = torch.from_numpy(w["cot"].astype(np.complex64)).pin_memory()
+        hout = torch.empty_like(hc).pin_memory()
+        dv, dc = torch.empty_like(vec0), torch.empty_like(cot0)
+
+        def step_e2e():
+            dv.copy_(hv, non_blocking=True)
+            dc.copy_(hc, non_blocking=True)
+            fsgpu.lucj_forward_(dv, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+            g = fsgpu.lucj_vjp_(dv, dc, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+            hout.copy_(dc, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return g
+
+        step_e2e()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.e2e_steps):
+            step_e2e()
+        b.record()
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / args.e2e_steps
+        grad_bytes = K.size * 16 + Jaa.size * 8 + Jab.size * 8
+        e2e = {"value": world * NLAYERS / (ems / 1e3), "unit": "layers/s",
+               "h2d_bytes_per_step": 2 * S, "d2h_bytes_per_step": S + grad_bytes,
+               "ms_per_step": ems}
+
+    # complex128, same workload, plain path on the same GPU
+    c128 = None
+    if args.c128_steps > 0:
+        v2 = torch.from_numpy(w["vec"]).cuda()
+        c2 = torch.from_numpy(w["cot"]).cuda()
+        cm = c2.clone()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fsgpu.lucj_forward_(v2, K, Jaa, Jab, NORB, NELEC, ctx=ctx)  # warm-up
+        out128 = v2.clone()
+        g128 = fsgpu.lucj_vjp_(v2, cm, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.c128_steps):
+            cm.copy_(c2)
+            fsgpu.lucj_forward_(v2, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+            fsgpu.lucj_vjp_(v2, cm, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+        b.record()
+        torch.cuda.synchronize()
+        cms = a.elapsed_time(b) / args.c128_steps
+        # c64 against c128 on the same inputs: forward output and gradients
+        v64 = vec0.clone()
+        fsgpu.lucj_forward_(v64, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+        fwd_err = float((v64.to(torch.complex128) - out128).abs().max().item())
+        c64 = cot0.clone()
+        g64 = fsgpu.lucj_vjp_(v64, c64, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+        rel = max(float(np.linalg.norm(x - y) / np.linalg.norm(y)) for x, y in zip(g64, g128))
+        c128 = {"layers_per_s": NLAYERS / (cms / 1e3), "ms_per_step": cms,
+                "c64_speedup": (NLAYERS / (cms / 1e3)) and value / world / (NLAYERS / (cms / 1e3)),
+                "c64_vs_c128_fwd_max_abs": fwd_err, "c64_vs_c128_grad_rel": rel}
+        del v2, c2, cm, out128, v64, c64
+
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (recs, tot_ms, kl) = top
+    per_launch_ms = tot_ms / recs
+    ab = algorithmic_bytes(name, S, NLAYERS)
+    roof = None
+    if ab is not None:
+        ach = ab / (per_launch_ms / 1e3) / 1e9
+        tr = recorded_traffic(name)
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                "traffic": tr, "algorithmic_bytes_per_launch": ab,
+                "ms_per_launch": per_launch_ms, "share_of_step": tot_ms / ms}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Haar rotations, N(0,0.5) couplings, random state)",
+        "config": {"workload": WORKLOAD, "norb": NORB, "nelec": list(NELEC),
+                   "layers": NLAYERS, "state": "complex64", "amplitudes": da * db,
+                   "l2": "inputs larger than L2 (%.2f GB state, 129 MB L2)" % (S / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "recovered_input_max_abs_err": rec_err, "c128": c128},
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "kernels": {k: {"records": v[0], "ms": v[1], "launches": v[2]} for k, v in prof.items()},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and not args.norb:
+        out["cpu_baseline"] = cpu_baseline(w)
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ oracle
+def cpu_baseline(w, budget_s=None):
+    """The oracle, as it stands, on a bounded sample of the workload, scaled
+    to layers/s by the oracle's own gate count per layer.
+
+    The oracle's LUCJ reverse mode per layer applies 4 orbital rotations
+    (U^dag and U forward, both again on the cotangent), each N(N-1)/2 = 120
+    Givens rotations per spin from its own decomposition; 2 transition
+    one-body reductions (one per rotation gate); 2 diagonal-Coulomb phase
+    evaluations.  Sample: 1 Givens rotation per spin on the full N=16
+    state, 1 diagonal-Coulomb evolution on the full state, and the
+    transition reduction on 16- and 32-vector slices of the state (alpha
+    part on column slices, beta part on row slices), extrapolated linearly
+    in the slice width."""
+    import oracle
+    from oracle import gates, lucj
+
+    norb, nelec = NORB, NELEC
+    v = w["vec"]
+    c = w["cot"]
+    t0 = time.perf_counter()
+    # Givens rotations (pairs are enumerated once, as the oracle caches them)
+    gates.givens_pairs(norb, 8, 0, 5)
+    gates.givens_pairs(norb, 8, 3, 11)
+    tg = []
+    for spin, (p, q) in ((0, (0, 5)), (1, (3, 11))):
+        t = time.perf_counter()
+        gates.apply_givens(v, 0.6, 0.8j, p, q, spin, norb, nelec)
+        tg.append(time.perf_counter() - t)
+    t = time.perf_counter()
+    oracle.apply_diag_coulomb_evolution(v, w["J_aa"][0], w["J_ab"][0], None, 1.0, norb, nelec)
+    tdc = time.perf_counter() - t
+    tt = []
+    for k in (16, 32):
+        t = time.perf_counter()
+        lucj.transition_one_body(c[:, :k], v[:, :k], norb, nelec, spins=(0,))
+        lucj.transition_one_body(c[:k, :], v[:k, :], norb, nelec, spins=(1,))
+        tt.append(time.perf_counter() - t)
+    # per-column slope and intercept of the reduction cost
+    slope = (tt[1] - tt[0]) / 16
+    t_T = max(tt[0] + slope * (math.comb(norb, 8) - 16), tt[1])
+    per_layer = 4 * 120 * (tg[0] + tg[1]) + 2 * t_T + 2 * tdc
+    return {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle",
+            "sample": ("1 Givens rotation per spin and 1 diagonal-Coulomb evolution on "
+                       "the full N=16 (8,8) complex128 state; the transition reduction on "
+                       "16- and 32-vector slices per spin, extrapolated linearly; composed "
+                       "by the oracle's per-layer gate count"),
+            "sample_seconds": time.perf_counter() - t0}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return
+    w = workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(w)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "layers/s",
+           "n_gpus": env_int("WORLD_SIZE", 1), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "norb": NORB, "nelec": list(NELEC),
+                      "layers": NLAYERS},
+           "cpu_baseline": {"value": v, "unit": "layers/s", "cores": 1, "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": "layers/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fsgpu", choices=["fsgpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--c128-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--norb", type=int, default=0,
+                    help="profiling only: another sector size instead of the N=16 workload")
+    ap.add_argument("--nalpha", type=int, default=0)
+    ap.add_argument("--nbeta", type=int, default=0)
+    ap.add_argument("--layers", type=int, default=NLAYERS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,15 @@ const char *fs_last_error(void);
  * itself failed. */
 int fs_sync_status(fs_ctx *ctx, void *stream);
 
+/* Kernel tracing.  fs_profile_start clears the record and brackets every
+ * following kernel launch of this context with CUDA events on its launch
+ * stream.  fs_profile_stop synchronizes those events, stops recording and
+ * writes a JSON object {"<step>": [records, total_ms, kernel_launches], ...}
+ * (NUL terminated) into out[0..cap); a record brackets one launch helper,
+ * which may launch several kernels.  FS_ERR_ARG if it does not fit. */
+int fs_profile_start(fs_ctx *ctx);
+int fs_profile_stop(fs_ctx *ctx, char *out, int64_t cap);
+
 /* Force or release the orbital-rotation method (default FS_ROT_AUTO). */
 int fs_set_rotation_path(fs_ctx *ctx, int path);
 

@@ -38,13 +38,14 @@ def lucj_forward(K, J_aa, J_ab, norb, nelec, vec=None):
     return psi
 
 
-def transition_one_body(g, psi, norb, nelec):
+def transition_one_body(g, psi, norb, nelec, spins=(0, 1)):
     """T[p, q] = <g| E_pq |psi> with E_pq = sum_sigma a^dag_{p sigma} a_{q sigma},
     computed string by string with the anticommutation sign of `excite`.
     The alpha operators anticommute past cre_b(I_b) twice, so they carry no
-    extra sign; the beta operators act directly on cre_b."""
+    extra sign; the beta operators act directly on cre_b.  `spins` limits
+    the sum to the listed spins (0 = alpha, 1 = beta)."""
     T = np.zeros((norb, norb), complex)
-    for spin in (0, 1):
+    for spin in spins:
         n = nelec[spin]
         s = strings(norb, n)
         amap = address_map(norb, n)

@@ -13,6 +13,25 @@ namespace fs {
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 
+Ctx*& current_ctx() {
+  static thread_local Ctx* c = nullptr;
+  return c;
+}
+void prof_begin(cudaStream_t st, cudaEvent_t* a) {
+  Ctx* c = current_ctx();
+  *a = nullptr;
+  if (!c || !c->prof_on) return;
+  if (cudaEventCreate(a) != cudaSuccess || cudaEventRecord(*a, st) != cudaSuccess) *a = nullptr;
+}
+void prof_end(const char* name, cudaStream_t st, cudaEvent_t a, int kernels) {
+  Ctx* c = current_ctx();
+  if (!a || !c) return;
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) return;
+  cudaEventRecord(b, st);
+  c->prof.push_back(ProfRec{name, a, b, kernels});
+}
+
 void* scratch(Ctx* ctx, const std::string& name, size_t bytes) {
   Scratch& s = ctx->scratch[name];
   if (s.bytes < bytes) {
@@ -237,6 +256,56 @@ int fs_sync_status(fs_ctx* ctx, void* stream) {
   return code;
 }
 
+int fs_profile_start(fs_ctx* ctx) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto& r : ctx->prof) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    ctx->prof.clear();
+    ctx->prof_on = true;
+  });
+}
+
+int fs_profile_stop(fs_ctx* ctx, char* out, int64_t cap) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr && out != nullptr && cap > 0, FS_ERR_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof_on = false;
+    struct Agg {
+      long n = 0, k = 0;
+      double ms = 0;
+    };
+    std::map<std::string, Agg> agg;
+    for (auto& r : ctx->prof) {
+      FS_CUDA(cudaEventSynchronize(r.b));
+      float ms = 0;
+      FS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto& x = agg[r.name];
+      x.n += 1;
+      x.k += r.kernels;
+      x.ms += ms;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    ctx->prof.clear();
+    std::string js = "{";
+    bool first = true;
+    for (auto& kv : agg) {
+      char buf[256];
+      snprintf(buf, sizeof buf, "%s\"%s\": [%ld, %.6f, %ld]", first ? "" : ", ",
+               kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.k);
+      js += buf;
+      first = false;
+    }
+    js += "}";
+    FS_REQUIRE((int64_t)js.size() < cap, FS_ERR_ARG, "profile buffer too small");
+    memcpy(out, js.c_str(), js.size() + 1);
+  });
+}
+
 int fs_set_rotation_path(fs_ctx* ctx, int path) {
   return guarded([&] {
     FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
@@ -251,6 +320,7 @@ int fs_string_table(fs_ctx* ctx, int norb, int nocc, uint32_t* masks_host, int64
     FS_REQUIRE(norb >= 0 && norb <= kMaxNorb && nocc >= 0 && nocc <= norb, FS_ERR_ARG,
                "bad (norb, nocc)");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     Space* s = get_space(ctx, norb, nocc, 0);
     FS_REQUIRE(dim == s->dim, FS_ERR_ARG, "dim must equal C(norb, nocc)");
@@ -264,6 +334,7 @@ int fs_excitation_table(fs_ctx* ctx, int norb, int nocc, uint32_t* out_host, int
     FS_REQUIRE(norb >= 1 && norb <= kMaxNorb && nocc >= 0 && nocc <= norb, FS_ERR_ARG,
                "bad (norb, nocc)");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     Space* s = get_space(ctx, norb, nocc, 0);
     FS_REQUIRE(n == s->dim * norb * norb, FS_ERR_ARG, "n_entries must be dim*norb*norb");
@@ -283,6 +354,7 @@ int fs_apply_orbital_rotation(fs_ctx* ctx, void* vec, int dtype, const double* U
     check_unitary(Ua, norb, "U_a");
     if (U_b) check_unitary(Ub, norb, "U_b");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Space* sa = get_space(ctx, norb, na, st);
@@ -301,6 +373,7 @@ int fs_apply_num_op_sum_evolution(fs_ctx* ctx, void* vec, int dtype, const doubl
     FS_REQUIRE(lam_a != nullptr, FS_ERR_ARG, "null lam_a");
     FS_REQUIRE(std::isfinite(t), FS_ERR_ARG, "t must be finite");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Space* sa = get_space(ctx, norb, na, st);
@@ -318,6 +391,7 @@ int fs_apply_diag_coulomb_evolution(fs_ctx* ctx, void* vec, int dtype, const dou
     FS_REQUIRE(J_aa != nullptr && J_ab != nullptr, FS_ERR_ARG, "null J_aa or J_ab");
     FS_REQUIRE(std::isfinite(t), FS_ERR_ARG, "t must be finite");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Space* sa = get_space(ctx, norb, na, st);
@@ -334,6 +408,7 @@ int fs_lucj_forward(fs_ctx* ctx, const fs_lucj* op, void* vec, int dtype, void* 
     const int n = op->norb, R = op->n_reps;
     const size_t nn = (size_t)n * n;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Space* sa = get_space(ctx, n, op->n_alpha, st);
@@ -492,6 +567,7 @@ extern "C" int fs_lucj_vjp(fs_ctx* ctx, const fs_lucj* op, void* vec, void* cot,
                "cotangent pointer must be non-null and 16-byte aligned");
     FS_REQUIRE(cot != vec, FS_ERR_ARG, "state and cotangent must be distinct buffers");
     std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     lucj_vjp_impl(ctx, op, vec, cot, dtype, dK, dJ_aa, dJ_ab, (cudaStream_t)stream);
   });

@@ -66,14 +66,38 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+  int kernels;
+};
+
 struct Ctx {
   int device = 0;
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
   cudaDeviceProp prop{};
   int rot_path = FS_ROT_AUTO;
   std::map<std::pair<int, int>, Space*> spaces;
   std::map<std::string, Scratch> scratch;
   int* d_status = nullptr;  // device status word
   std::mutex mu;
+};
+
+// Kernel tracing: when the current context has profiling on, every launch
+// helper brackets its kernel with CUDA events on the launch stream.
+Ctx*& current_ctx();
+void prof_begin(cudaStream_t st, cudaEvent_t* a);
+void prof_end(const char* name, cudaStream_t st, cudaEvent_t a, int kernels);
+struct ProfScope {  // brackets `kernels` kernel launches
+  const char* name;
+  cudaStream_t st;
+  int kernels;
+  cudaEvent_t a = nullptr;
+  ProfScope(const char* n, cudaStream_t s, int k = 1) : name(n), st(s), kernels(k) {
+    prof_begin(st, &a);
+  }
+  ~ProfScope() { prof_end(name, st, a, kernels); }
 };
 
 Space* get_space(Ctx* ctx, int norb, int nocc, cudaStream_t st);

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kRThreads)
 
 void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,
                     double* dJ_aa, double* dJ_ab, cudaStream_t st) {
+  ProfScope ps("dc_grad", st, 3);
   const int norb = sa->norb;
   const int sms = ctx->prop.multiProcessorCount;
   unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 2 * sms);

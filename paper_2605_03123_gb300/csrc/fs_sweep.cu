@@ -346,6 +346,10 @@ static void launch_sweep_t(const SweepGeom& g, const GProg<R>& prog, const Mat& 
   auto kern = k_sweep<R, CS, NST, VJP>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
+  static const char* names[2][2][2] = {
+      {{"sweep_alpha_f32", "sweep_beta_f32"}, {"sweep_vjp_alpha_f32", "sweep_vjp_beta_f32"}},
+      {{"sweep_alpha_f64", "sweep_beta_f64"}, {"sweep_vjp_alpha_f64", "sweep_vjp_beta_f64"}}};
+  ProfScope ps(names[sizeof(R) == 8][VJP][g.dir], st);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nslabs * CS));
   cfg.blockDim = dim3(kThreads);
@@ -476,6 +480,7 @@ __global__ void __launch_bounds__(256)
 
 void launch_phase(const Space* sa, const Space* sb, void* vec, int dtype,
                   const PhaseDev& ph, cudaStream_t st) {
+  ProfScope ps(dtype == FS_C64 ? "phase_f32" : "phase_f64", st);
   int nchunk = (sa->norb + 7) / 8;
   unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 4096);
   if (dtype == FS_C64)
@@ -518,6 +523,7 @@ __global__ void k_string_phase(cx_t<R>* out, const uint32_t* masks, int64_t dim,
 
 void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& f,
                          cudaStream_t st) {
+  ProfScope ps("string_phase", st);
   unsigned grid = (unsigned)((sp->dim + 127) / 128);
   if (dtype == FS_C64)
     k_string_phase<float><<<grid, 128, 0, st>>>((float2*)out, sp->masks, sp->dim,
@@ -589,6 +595,7 @@ __global__ void k_outer(cx_t<R>* vec, const double2* va, const double2* vb, int6
 
 void launch_slater(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dtype,
                    const CMat& R, cudaStream_t st) {
+  ProfScope ps("slater", st, 3);
   double2* va = (double2*)scratch(ctx, "slater_a", sa->dim * 16);
   double2* vb = (double2*)scratch(ctx, "slater_b", sb->dim * 16);
   k_slater_minors<<<(unsigned)((sa->dim + 63) / 64), 64, 0, st>>>(

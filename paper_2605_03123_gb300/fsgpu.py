@@ -48,6 +48,8 @@ SIGNATURES = {
     "fs_last_error": [],
     "fs_sync_status": [_P, _P],
     "fs_set_rotation_path": [_P, _I],
+    "fs_profile_start": [_P],
+    "fs_profile_stop": [_P, ctypes.c_char_p, _I64],
     "fs_string_table": [_P, _I, _I, _P, _I64],
     "fs_excitation_table": [_P, _I, _I, _P, _I64],
     "fs_apply_orbital_rotation": [_P, _P, _I, _P, _P, _I, _I, _I, _P],
@@ -102,6 +104,16 @@ class Context:
 
     def set_rotation_path(self, path):
         _check("fs_set_rotation_path", load_library().fs_set_rotation_path(self.handle, int(path)))
+
+    def profile_start(self):
+        _check("fs_profile_start", load_library().fs_profile_start(self.handle))
+
+    def profile_stop(self):
+        """{step: (records, total_ms, kernel_launches)} since profile_start."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check("fs_profile_stop", load_library().fs_profile_stop(self.handle, buf, len(buf)))
+        return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
 
     def sync_status(self, stream=None):
         return load_library().fs_sync_status(self.handle, _stream_ptr(stream))

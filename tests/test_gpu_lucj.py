@@ -71,3 +71,127 @@ def test_lucj_zero_reps_from_hf(lib):
     z = np.zeros((0, 6, 6))
     lib.lucj_forward_(x, z, z, z, 6, (3, 3), from_hf=True)
     assert np.array_equal(host(x), oracle.hartree_fock(6, (3, 3)))
+
+
+# ---------------------------------------------------------------------- VJP
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _small_case(norb, nelec, n_reps, seed, from_hf):
+    g = inputs.rng(seed)
+    K = np.array([inputs.random_antihermitian(norb, 0.5, g) for _ in range(n_reps)])
+    Jaa = np.array([inputs.random_symmetric(norb, 0.5, g) for _ in range(n_reps)])
+    Jab = np.array([g.normal(0, 0.5, (norb, norb)) for _ in range(n_reps)])
+    v = None if from_hf else inputs.random_state(norb, nelec, g)
+    c = inputs.random_state(norb, nelec, g)
+    return K, Jaa, Jab, v, c
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("norb,nelec,n_reps,from_hf", [
+    (6, (3, 2), 2, False), (5, (2, 3), 3, False), (6, (3, 3), 2, True), (4, (4, 1), 2, False),
+    (2, (1, 1), 1, False), (7, (0, 3), 2, False), (8, (4, 4), 1, True)])
+def test_lucj_vjp_small_against_oracle(lib, dt, norb, nelec, n_reps, from_hf):
+    K, Jaa, Jab, v, c = _small_case(norb, nelec, n_reps, 12000 + norb * 7 + n_reps, from_hf)
+    rK, rJa, rJb, rv = oracle.lucj_vjp(K, Jaa, Jab, c, norb, nelec, vec=v)
+    x = dev(oracle.hartree_fock(norb, nelec) if from_hf else v, dt)
+    lib.lucj_forward_(x, K, Jaa, Jab, norb, nelec, from_hf=from_hf)
+    cg = dev(c, dt)
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec, from_hf=from_hf)
+    tol = 1e-11 if dt == "c128" else 2e-4
+    assert _rel(dK, rK) < tol and _rel(dJa, rJa) < tol and _rel(dJb, rJb) < tol
+    v_in = oracle.hartree_fock(norb, nelec) if from_hf else v
+    assert np.max(np.abs(host(x) - v_in)) < TOL[dt]            # uncomputed input
+    if not from_hf:
+        assert np.max(np.abs(host(cg) - rv)) < TOL[dt]         # dL/dpsi_in
+
+
+@pytest.fixture(scope="module")
+def lucj_small_vjp_ref(lucj_small_ref):
+    w, ref = lucj_small_ref
+    r = oracle.lucj_vjp(w["K"], w["J_aa"], w["J_ab"], w["cot"], w["norb"], w["nelec"])
+    return w, ref, r
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_lucj_vjp_n12_against_oracle(lib, dt, lucj_small_vjp_ref):
+    """N=12 (6,6), 4 repetitions from Hartree-Fock: gradients within 1e-6
+    relative of the oracle's stored-state reverse mode in complex128."""
+    w, ref, (rK, rJa, rJb, rv) = lucj_small_vjp_ref
+    norb, nelec = w["norb"], w["nelec"]
+    x = dev(np.zeros((924, 924)), dt)
+    lib.lucj_forward_(x, w["K"], w["J_aa"], w["J_ab"], norb, nelec, from_hf=True)
+    cg = dev(w["cot"], dt)
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, w["K"], w["J_aa"], w["J_ab"], norb, nelec, from_hf=True)
+    tol = 1e-6 if dt == "c128" else 1e-3
+    for a, b in ((dK, rK), (dJa, rJa), (dJb, rJb)):
+        assert _rel(a, b) < tol
+    assert np.max(np.abs(host(x) - oracle.hartree_fock(norb, nelec))) < TOL[dt]
+
+
+def test_lucj_vjp_n12_central_differences(lib, lucj_small_ref):
+    """Central differences (step 1e-6) of the GPU forward pass in complex128
+    along random anti-Hermitian / symmetric directions, against the VJP."""
+    w, _ = lucj_small_ref
+    norb, nelec = w["norb"], w["nelec"]
+    K, Jaa, Jab, cot = w["K"], w["J_aa"], w["J_ab"], w["cot"]
+
+    def loss(K_, Ja_, Jb_):
+        x = dev(np.zeros((924, 924)), "c128")
+        lib.lucj_forward_(x, K_, Ja_, Jb_, norb, nelec, from_hf=True)
+        return float(np.real(np.vdot(cot, host(x))))
+
+    x = dev(np.zeros((924, 924)), "c128")
+    lib.lucj_forward_(x, K, Jaa, Jab, norb, nelec, from_hf=True)
+    dK, dJa, dJb = lib.lucj_vjp_(x, dev(cot, "c128"), K, Jaa, Jab, norb, nelec, from_hf=True)
+    g = inputs.rng(31337)
+    h = 1e-6
+    for trial in range(3):
+        eK = np.array([inputs.random_antihermitian(norb, 1.0, g) for _ in range(len(K))])
+        eA = np.array([inputs.random_symmetric(norb, 1.0, g) for _ in range(len(K))])
+        eB = np.array([g.normal(0, 1, (norb, norb)) for _ in range(len(K))])
+        fd = (loss(K + h * eK, Jaa + h * eA, Jab + h * eB)
+              - loss(K - h * eK, Jaa - h * eA, Jab - h * eB)) / (2 * h)
+        an = (np.sum(dK.real * eK.real + dK.imag * eK.imag) + np.sum(dJa * eA)
+              + np.sum(dJb * eB))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (trial, fd, an)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_lucj_vjp_full_size_properties(lib, dt):
+    """N=16 (8,8), 2 layers of the metric workload: the reverse sweeps recover
+    the input state, and dL/dpsi_in = C^dag g satisfies <C^dag g, psi_in> =
+    <g, psi_out> with unit norm (C unitary)."""
+    w = inputs.lucj_layers(16, (8, 8), 2, 0.5, 0.3, 2000 + 5)
+    norb, nelec = 16, (8, 8)
+    x = dev(w["vec"], dt)
+    lib.lucj_forward_(x, w["K"], w["J_aa"], w["J_ab"], norb, nelec)
+    out = host(x)
+    cg = dev(w["cot"], dt)
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, w["K"], w["J_aa"], w["J_ab"], norb, nelec)
+    rec, dv = host(x), host(cg)
+    tol = TOL[dt] if dt == "c128" else 2e-5
+    assert np.max(np.abs(rec - w["vec"])) < tol
+    lhs, rhs = np.vdot(dv, w["vec"]), np.vdot(w["cot"], out)
+    assert abs(lhs - rhs) < (1e-11 if dt == "c128" else 1e-4)
+    assert abs(np.linalg.norm(dv) - 1) < (1e-11 if dt == "c128" else 1e-4)
+    assert np.all(np.isfinite(dK)) and np.all(np.isfinite(dJa)) and np.all(np.isfinite(dJb))
+
+
+def test_autograd_function_matches_oracle(lib):
+    from paper_2605_03123_gb300.autograd import lucj
+    norb, nelec, n_reps = 6, (3, 2), 2
+    K, Jaa, Jab, v, c = _small_case(norb, nelec, n_reps, 777, False)
+    rK, rJa, rJb, rv = oracle.lucj_vjp(K, Jaa, Jab, c, norb, nelec, vec=v)
+    vt = dev(v, "c128").requires_grad_(True)
+    Kt = torch.from_numpy(K).requires_grad_(True)
+    At = torch.from_numpy(Jaa).requires_grad_(True)
+    Bt = torch.from_numpy(Jab).requires_grad_(True)
+    out = lucj(vt, Kt, At, Bt, norb, nelec)
+    loss = torch.real(torch.vdot(dev(c, "c128").flatten(), out.flatten()))
+    loss.backward()
+    assert np.max(np.abs(Kt.grad.numpy() - rK)) < 1e-11
+    assert np.max(np.abs(At.grad.numpy() - rJa)) < 1e-11
+    assert np.max(np.abs(Bt.grad.numpy() - rJb)) < 1e-11
+    assert np.max(np.abs(host(vt.grad) - rv)) < 1e-12
