@@ -8,16 +8,20 @@ namespace fs {
 
 __constant__ uint32_t c_binom[kMaxOrb + 1][kMaxOrb + 1];
 
+// Constant memory is per device: upload the table once for each device
+// this process uses (the current device at the time of the call).
 static void upload_binomials() {
-  static bool done = false;
   static std::mutex m;
+  static bool done[256] = {};
+  int dev = 0;
+  FS_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> g(m);
-  if (done) return;
+  if (dev >= 0 && dev < 256 && done[dev]) return;
   uint32_t h[kMaxOrb + 1][kMaxOrb + 1];
   for (int n = 0; n <= kMaxOrb; ++n)
     for (int k = 0; k <= kMaxOrb; ++k) h[n][k] = (uint32_t)binom_host(n, k);
   FS_CUDA(cudaMemcpyToSymbol(c_binom, h, sizeof(h)));
-  done = true;
+  if (dev >= 0 && dev < 256) done[dev] = true;
 }
 
 __device__ __forceinline__ uint32_t cns_rank(uint32_t mask) {
