@@ -136,6 +136,34 @@ int fs_apply_diag_coulomb_evolution(fs_ctx *ctx, void *vec, int dtype,
                                     const double *J_bb, double t, int norb,
                                     int n_alpha, int n_beta, void *stream);
 
+/* The same diagonal-Coulomb evolution for callers that must not allocate
+ * device memory: callers whose device memory belongs to a pool or arena the
+ * library may not bypass, and callers that cannot afford the device-wide
+ * synchronization a cudaMalloc or cudaFree can cause.  The paper has no
+ * counterpart; this is a deployment variant of the call above.
+ *
+ * Needs no context and allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine): its scratch (string masks and per-string
+ * phase factors, 640 KiB) is one static device array that every GPU which
+ * loads the library holds until the process exits.  The caller still owns
+ * `vec`.  Arguments and results are those of
+ * fs_apply_diag_coulomb_evolution; each spin may have at most 16384 strings
+ * (C(norb, n) <= 16384), larger sectors return FS_ERR_UNSUPPORTED before any
+ * work is enqueued.
+ *
+ * The first call on a device looks up the array's device address and
+ * uploads a small constant table with that device current; make that first
+ * call before any stream capture.  All calls share the one array and
+ * overwrite all of it that they read, so nothing carries over between calls;
+ * calls that overlap on the GPU (on different streams, or from different
+ * host threads without ordering) race on it. */
+int fs_apply_diag_coulomb_evolution_noalloc(void *vec, int dtype,
+                                            const double *J_aa,
+                                            const double *J_ab,
+                                            const double *J_bb, double t,
+                                            int norb, int n_alpha, int n_beta,
+                                            void *stream);
+
 /* LUCJ ansatz (§4.3, §4.5.1): n_reps repetitions U_k D_k U_k^dag, k = 0 ..
  * n_reps-1 applied in order, with U_k = U(expm(K_k)) (K_k anti-Hermitian,
  * N x N complex) and D_k the spin-balanced diagonal-Coulomb evolution with

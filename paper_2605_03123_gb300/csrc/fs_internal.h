@@ -193,5 +193,7 @@ void launch_slater(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dt
                    const CMat& R, cudaStream_t st);
 
 void launch_exc_table(const Space* sp, uint32_t* out, cudaStream_t st);
+// masks[dim] of the strings of nocc electrons in norb orbitals, into `out`.
+void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st);
 
 }  // namespace fs

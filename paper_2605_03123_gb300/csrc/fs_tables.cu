@@ -192,6 +192,13 @@ void free_space(Space* s) {
   delete s;
 }
 
+void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st) {
+  upload_binomials();
+  int64_t dim = choose(norb, nocc);
+  k_masks<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(out, dim, nocc, norb);
+  FS_CUDA(cudaGetLastError());
+}
+
 void launch_exc_table(const Space* sp, uint32_t* out, cudaStream_t st) {
   k_exc_table<<<(unsigned)((sp->dim + 127) / 128), 128, 0, st>>>(
       out, sp->masks, sp->dim, sp->norb);

@@ -55,6 +55,7 @@ SIGNATURES = {
     "fs_apply_orbital_rotation": [_P, _P, _I, _P, _P, _I, _I, _I, _P],
     "fs_apply_num_op_sum_evolution": [_P, _P, _I, _P, _P, _D, _I, _I, _I, _P],
     "fs_apply_diag_coulomb_evolution": [_P, _P, _I, _P, _P, _P, _D, _I, _I, _I, _P],
+    "fs_apply_diag_coulomb_evolution_noalloc": [_P, _I, _P, _P, _P, _D, _I, _I, _I, _P],
     "fs_lucj_forward": [_P, ctypes.POINTER(LUCJ), _P, _I, _P],
     "fs_lucj_vjp": [_P, ctypes.POINTER(LUCJ), _P, _P, _I, _P, _P, _P, _P],
 }
@@ -233,6 +234,21 @@ def apply_diag_coulomb_evolution_(vec, J_aa, J_ab, t, norb, nelec, J_bb=None, ct
 
 def apply_diag_coulomb_evolution(vec, J_aa, J_ab, t, norb, nelec, J_bb=None, ctx=None):
     return apply_diag_coulomb_evolution_(vec.clone(), J_aa, J_ab, t, norb, nelec, J_bb, ctx)
+
+
+def apply_diag_coulomb_evolution_noalloc_(vec, J_aa, J_ab, t, norb, nelec, J_bb=None):
+    """In-place diagonal-Coulomb evolution that allocates no device memory
+    (for callers that must not allocate; at most 16384 strings per spin).
+    Uses the current device and stream; needs no context."""
+    _check_state(vec, norb, nelec)
+    a = _f64(J_aa, (norb, norb))
+    b = _f64(J_ab, (norb, norb))
+    c = None if J_bb is None else _f64(J_bb, (norb, norb))
+    _check("fs_apply_diag_coulomb_evolution_noalloc",
+           load_library().fs_apply_diag_coulomb_evolution_noalloc(
+               _P(vec.data_ptr()), _dtype_code(vec), _ptr(a), _ptr(b), _ptr(c), float(t),
+               norb, nelec[0], nelec[1], _stream_ptr()))
+    return vec
 
 
 # ------------------------------------------------------------------- LUCJ
