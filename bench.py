@@ -147,6 +147,25 @@ def algorithmic_bytes(kernel, S, n_layers):
     return None
 
 
+def algorithmic_flops(kernel, norb, nelec, amplitudes):
+    """FP32 (or FP64) flops the method needs per launch of a sweep: 12 flops
+    per element-Givens (two complex rotations of an amplitude pair are 24
+    real FMA-flops per pair), N(N-1)/2 rotations each touching the fraction
+    2 C(N-2, n-1) / C(N, n) of the strings; the reverse sweep rotates two
+    states and adds the transition reduction, n(N-n) + n complex
+    multiply-adds (8 flops) per amplitude and spin."""
+    spin = 0 if "alpha" in kernel else 1
+    n = nelec[spin]
+    N = norb
+    if not kernel.startswith("sweep") or n < 1 or N < 2:
+        return None
+    eg = N * (N - 1) / 2 * 2 * math.comb(N - 2, n - 1) / math.comb(N, n)
+    per = 12 * eg
+    if "vjp" in kernel:
+        per = 2 * per + 8 * (n * (N - n) + n)
+    return per * amplitudes
+
+
 def run_gpu(args):
     import torch
     from paper_2605_03123_gb300 import fsgpu
@@ -284,6 +303,16 @@ def run_gpu(args):
                 "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak,
                 "traffic": tr, "algorithmic_bytes_per_launch": ab,
                 "ms_per_launch": per_launch_ms, "share_of_step": tot_ms / ms}
+        fl = algorithmic_flops(name, NORB, NELEC, da * db)
+        csum = clk.summary()
+        if fl is not None and csum:
+            # FP32 FMA peak from the unit counts: 152 SMs x 128 lanes x 2 flops
+            # per clock at the SM clock sampled during the timed region
+            fpeak = 152 * 128 * 2 * csum["sm_mhz"] * 1e6 / 1e12
+            fach = fl / (per_launch_ms / 1e3) / 1e12
+            roof["alu"] = {"achieved": fach, "peak": fpeak, "unit": "TFLOP/s",
+                           "frac": fach / fpeak, "algorithmic_flops_per_launch": fl,
+                           "peak_source": "unit counts x sampled SM clock (FP32 FMA)"}
 
     out = {
         "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world,

@@ -134,4 +134,103 @@ RotProgram decompose_adjacent(int n, const zd* U) {
   return prog;
 }
 
+// Greedy grouping of a Givens sequence into window steps: repeatedly take
+// the window [a, a+W) that admits the most rotations whose earlier
+// neighbours (rotations sharing an orbital and preceding them) are done or
+// taken in the same step; the taken rotations keep their relative order, so
+// the product of all rotations is unchanged.
+std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W) {
+  const int M = (int)rp.g.size();
+  std::vector<char> done(M, 0);
+  std::vector<WinStep> steps;
+  std::vector<int> taken;
+  int nd = 0;
+  while (nd < M) {
+    WinStep best{0, {}};
+    for (int a = 0; a + W <= N; ++a) {
+      taken.clear();
+      uint64_t blocked = 0;
+      for (int k = 0; k < M; ++k) {
+        if (done[k]) continue;
+        const int p = rp.g[k].p;
+        const uint64_t ob = 3ull << p;
+        if (ob & blocked) {
+          blocked |= ob;
+          continue;
+        }
+        if (p >= a && p + 1 < a + W)
+          taken.push_back(k);
+        else
+          blocked |= ob;
+      }
+      if (taken.size() > best.givens.size()) best = WinStep{a, taken};
+    }
+    for (int k : best.givens) done[k] = 1;
+    nd += (int)best.givens.size();
+    steps.push_back(best);
+  }
+  return steps;
+}
+
+// For the window [a, a+W): every outside configuration O with
+// m = n - |O| in 1 .. W-1 is one orbit.  With c_lo = |O below a|, the address
+// of O u S (S inside the window) is R_O + F[a][c_lo][S], where R_O sums
+// C(o_k, k+1) over O's orbitals with their index k in the full string and F
+// sums the same terms over S's orbitals (combinatorial-number-system rank).
+void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
+                        std::vector<int>& off, std::vector<uint16_t>& offs) {
+  const int npos = N - W + 1;
+  orbits.clear();
+  off.assign(npos + 1, 0);
+  offs.assign((size_t)npos * (n + 1) << W, 0);
+  auto C = [](int a, int b) -> uint64_t {
+    if (b < 0 || b > a) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (uint64_t)(a - b + i) / (uint64_t)i;
+    return r;
+  };
+  for (int a = 0; a < npos; ++a) {
+    off[a] = (int)orbits.size();
+    std::vector<int> out;
+    for (int p = 0; p < N; ++p)
+      if (p < a || p >= a + W) out.push_back(p);
+    const int no = (int)out.size();
+    for (int m = 1; m < W; ++m) {
+      const int ne = n - m;
+      if (ne < 0 || ne > no) continue;
+      // ne-subsets of the outside orbitals, ascending masks (Gosper's hack)
+      uint64_t x = ne == 0 ? 0 : ((1ull << ne) - 1);
+      while (true) {
+        int clo = 0, k = 0;
+        uint64_t ro = 0;
+        for (int i = 0; i < no; ++i)
+          if ((x >> i) & 1) {
+            int o = out[i];
+            if (o < a) {
+              ro += C(o, k + 1);
+              ++clo;
+            } else {
+              ro += C(o, k + m + 1);
+            }
+            ++k;
+          }
+        orbits.push_back((uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
+        if (ne == 0) break;
+        uint64_t c = x & (~x + 1), r = x + c;
+        x = (((r ^ x) >> 2) / c) | r;
+        if (x >> no) break;
+      }
+    }
+    for (int clo = 0; clo <= n; ++clo)
+      for (int S = 0; S < (1 << W); ++S) {
+        uint64_t f = 0;
+        int j = 0;
+        for (int b = 0; b < W; ++b)
+          if ((S >> b) & 1) f += C(a + b, clo + (j++) + 1);
+        offs[(((size_t)a * (n + 1) + clo) << W) + S] = (uint16_t)std::min<uint64_t>(f, 65535);
+      }
+  }
+  off[npos] = (int)orbits.size();
+}
+
 }  // namespace fs

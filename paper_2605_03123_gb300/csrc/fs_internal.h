@@ -45,6 +45,21 @@ void expm_frechet_adjoint(int n, const zd* K, const zd* H, zd* out);
 double unitarity_error(int n, const zd* U);
 RotProgram decompose_adjacent(int n, const zd* U);
 
+// Window steps of a Givens program: step s applies the listed rotations
+// (indices into RotProgram::g, in program order), all acting on orbitals
+// inside [a, a + W).
+struct WinStep {
+  int a;
+  std::vector<int> givens;
+};
+std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W);
+// Orbit tables of the strings of n electrons in N orbitals for windows of W
+// adjacent orbitals: for each window position a, orbits[off[a] .. off[a+1])
+// hold R_O | c_lo << 16 | m << 24 (sorted by m), and
+// offs[((a * (n+1) + c_lo) << W) + S] is the in-window rank offset.
+void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
+                        std::vector<int>& off, std::vector<uint16_t>& offs);
+
 // ------------------------------------------------------ device tables
 // Per-sector-spin tables: strings of `nocc` electrons in `norb` orbitals.
 struct Space {
@@ -59,6 +74,15 @@ struct Space {
   uint32_t* xsign = nullptr;   // [norb*norb][ceil(nx/32)] sign bits
   int nx = 0;                  // entries per (p, q) list (max over p, q)
   int* xcount = nullptr;       // [norb*norb] actual entries per list
+  // window tables for the register-blocked sweeps, per window width W:
+  // orbit descriptors R_O | c_lo << 16 | m << 24 grouped by window position
+  // and sorted by m, and in-window rank offsets F[a][c_lo][S]
+  struct Win {
+    uint32_t* orbits = nullptr;
+    int* off = nullptr;
+    uint16_t* offs = nullptr;
+    bool built = false;
+  } win[8];
 };
 
 struct Scratch {

@@ -18,6 +18,9 @@ constexpr int kRThreads = 256;
 // Rows: V_i[q] = sum_j W_ij occ_b(j)_q and r_i = sum_j W_ij; then
 // dJ_ab[p][q] += occ_a(i)_p V_i[q] and dJ_aa[p][q] += 1/2 r_i occ_a(i)_p occ_a(i)_q,
 // accumulated per CTA in shared memory and flushed once.
+// Per-thread partial sums run in the precision of W (FP32 for complex64
+// states, where FP64 arithmetic would be 1/64-rate); the block reduction and
+// the accumulators are FP64.
 template <typename R, int NQ>
 __global__ void __launch_bounds__(kRThreads)
     k_dc_rows(const R* W, int64_t da, int64_t db, const uint32_t* ma, const uint32_t* mb,
@@ -28,18 +31,22 @@ __global__ void __launch_bounds__(kRThreads)
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t i = blockIdx.x; i < da; i += gridDim.x) {
-    double acc[NQ];
-    double r = 0;
+    R pacc[NQ];
+    R pr = 0;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0;
+    for (int q = 0; q < NQ; ++q) pacc[q] = 0;
     const R* row = W + i * db;
     for (int64_t j = threadIdx.x; j < db; j += kRThreads) {
-      double w = (double)row[j];
+      R w = row[j];
       uint32_t m = __ldg(mb + j);
-      r += w;
+      pr += w;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[q] += ((m >> q) & 1u) ? w : 0.0;
+      for (int q = 0; q < NQ; ++q) pacc[q] += ((m >> q) & 1u) ? w : (R)0;
     }
+    double acc[NQ];
+    double r = (double)pr;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = (double)pacc[q];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
@@ -82,29 +89,30 @@ __global__ void k_dc_cols(const R* W, int64_t da, int64_t db, int rows_per, doub
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= db) return;
   int64_t i0 = (int64_t)blockIdx.y * rows_per, i1 = min(da, i0 + rows_per);
-  double s = 0;
-  for (int64_t i = i0; i < i1; ++i) s += (double)W[i * db + j];
-  atomicAdd(c + j, s);
+  R s = 0;
+#pragma unroll 8
+  for (int64_t i = i0; i < i1; ++i) s += W[i * db + j];
+  atomicAdd(c + j, (double)s);
 }
 
-// dJ_aa[p][q] += 1/2 sum_j c_j occ_b(j)_p occ_b(j)_q.
+// dJ_aa[p][q] += 1/2 sum_j c_j occ_b(j)_p occ_b(j)_q; one block per (p, q).
 __global__ void __launch_bounds__(kRThreads)
     k_dc_beta_aa(const double* c, int64_t db, const uint32_t* mb, int norb, double* dJaa) {
-  __shared__ double s[kMaxOrb * kMaxOrb];
-  for (int k = threadIdx.x; k < norb * norb; k += kRThreads) s[k] = 0;
+  __shared__ double red[kRThreads / 32];
+  const int p = blockIdx.x / norb, q = blockIdx.x % norb;
+  const uint32_t want = (1u << p) | (1u << q);
+  double s = 0;
+  for (int64_t j = threadIdx.x; j < db; j += kRThreads)
+    if ((__ldg(mb + j) & want) == want) s += c[j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int64_t j = blockIdx.x * (int64_t)kRThreads + threadIdx.x; j < db;
-       j += (int64_t)gridDim.x * kRThreads) {
-    uint32_t m = mb[j];
-    double v = 0.5 * c[j];
-    for (uint32_t a = m; a; a &= a - 1) {
-      int p = __ffs(a) - 1;
-      for (uint32_t b = m; b; b &= b - 1) atomicAdd(&s[p * norb + __ffs(b) - 1], v);
-    }
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < kRThreads / 32; ++k) t += red[k];
+    dJaa[blockIdx.x] += 0.5 * t;
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < norb * norb; k += kRThreads)
-    if (s[k] != 0) atomicAdd(dJaa + k, s[k]);
 }
 
 void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,
@@ -131,15 +139,14 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
   FS_CUDA(cudaGetLastError());
   double* c = (double*)scratch(ctx, "dc_colsum", sb->dim * sizeof(double));
   FS_CUDA(cudaMemsetAsync(c, 0, sb->dim * sizeof(double), st));
-  const int rows_per = 256;
+  const int rows_per = 64;
   dim3 g2((unsigned)((sb->dim + 255) / 256), (unsigned)((sa->dim + rows_per - 1) / rows_per));
   if (dtype == FS_C64)
     k_dc_cols<float><<<g2, 256, 0, st>>>((const float*)W, sa->dim, sb->dim, rows_per, c);
   else
     k_dc_cols<double><<<g2, 256, 0, st>>>((const double*)W, sa->dim, sb->dim, rows_per, c);
   FS_CUDA(cudaGetLastError());
-  unsigned g3 = (unsigned)std::min<int64_t>((sb->dim + kRThreads - 1) / kRThreads, sms);
-  k_dc_beta_aa<<<g3, kRThreads, 0, st>>>(c, sb->dim, sb->masks, norb, dJ_aa);
+  k_dc_beta_aa<<<norb * norb, kRThreads, 0, st>>>(c, sb->dim, sb->masks, norb, dJ_aa);
   FS_CUDA(cudaGetLastError());
 }
 

@@ -12,6 +12,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "fs_common.cuh"
 #include "fs_internal.h"
@@ -27,6 +29,20 @@ template <typename R>
 struct GProg {
   int m;
   int8_t p[kMaxGivens];
+  R c[kMaxGivens];
+  R sr[kMaxGivens];
+  R si[kMaxGivens];
+};
+
+// Window program: step s applies Givens g0[s] .. g0[s+1]-1, all acting on
+// orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
+// index of the rotated pair (p, p+1).
+template <typename R>
+struct WProg {
+  int nsteps;
+  int8_t a[kMaxGivens];
+  int16_t g0[kMaxGivens + 1];
+  int8_t u[kMaxGivens];
   R c[kMaxGivens];
   R sr[kMaxGivens];
   R si[kMaxGivens];
@@ -58,6 +74,147 @@ struct SweepGeom {
   int nx;
   double* T;  // [norb][norb] complex accumulator: += <g| E_pq |psi>
   void* W;    // [d_a][d_b] real: Im(conj(g) psi), or null
+  // window tables of the rotated spin (window kernels only)
+  const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
+  const int* orb_off;      // [npos + 1] start of each position's list
+  const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
+  int offs_stride;         // (nocc + 1) << W
+};
+
+// Subsets of a W-orbital window holding M electrons, in ascending-mask
+// order, and for every local adjacent pair (u, u+1) the index pairs
+// (S, S') with u in S, u+1 not in S and S' = S - {u} + {u+1}.
+__host__ __device__ constexpr int cbinom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  int r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+__host__ __device__ constexpr int cpopc(int x) {
+  int c = 0;
+  while (x) {
+    c += x & 1;
+    x >>= 1;
+  }
+  return c;
+}
+// k-th W-bit mask with M bits set, in ascending order.
+__host__ __device__ constexpr int win_mask(int W, int M, int k) {
+  for (int x = 0; x < (1 << W); ++x)
+    if (cpopc(x) == M && k-- == 0) return x;
+  return -1;
+}
+__host__ __device__ constexpr int win_index(int W, int M, int mask) {
+  int k = 0;
+  for (int x = 0; x < mask; ++x) k += cpopc(x) == M;
+  return k;
+}
+// The j-th pair (S, S') of local rotation u: S has u and not u+1.
+__host__ __device__ constexpr int win_src_mask(int W, int M, int u, int j) {
+  for (int x = 0; x < (1 << W); ++x)
+    if (cpopc(x) == M && ((x >> u) & 1) && !((x >> (u + 1)) & 1) && j-- == 0) return x;
+  return -1;
+}
+__host__ __device__ constexpr int win_npairs(int W, int M, int u) {
+  int n = 0;
+  for (int x = 0; x < (1 << W); ++x) n += cpopc(x) == M && ((x >> u) & 1) && !((x >> (u + 1)) & 1);
+  return n;
+}
+
+template <int W, int M, int U, int J, typename R, int NV, int NS>
+__device__ __forceinline__ void win_pair(cx_t<R> (&v)[NV][NS], R c, R sr, R si) {
+  constexpr int sm = win_src_mask(W, M, U, J);
+  constexpr int a = win_index(W, M, sm);
+  constexpr int b = win_index(W, M, sm ^ (1 << U) ^ (1 << (U + 1)));
+#pragma unroll
+  for (int x = 0; x < NV; ++x) givens2<R>(v[x][a], v[x][b], c, sr, si);
+}
+template <int W, int M, int U, typename R, int NV, int NS, int... J>
+__device__ __forceinline__ void win_pairs_seq(cx_t<R> (&v)[NV][NS], R c, R sr, R si,
+                                              std::integer_sequence<int, J...>) {
+  (win_pair<W, M, U, J, R, NV, NS>(v, c, sr, si), ...);
+}
+template <int W, int M, int U, typename R, int NV, int NS>
+__device__ __forceinline__ void win_pairs(cx_t<R> (&v)[NV][NS], R c, R sr, R si) {
+  if constexpr (U + 1 < W)
+    win_pairs_seq<W, M, U, R, NV, NS>(v, c, sr, si,
+                                      std::make_integer_sequence<int, win_npairs(W, M, U)>{});
+}
+
+template <int W, int M, int K>
+__device__ __forceinline__ int win_offset(const uint16_t* Fc) {
+  constexpr int mk = win_mask(W, M, K);
+  return __ldg(Fc + mk);
+}
+template <int W, int M, int... K>
+__device__ __forceinline__ void win_offsets(const uint16_t* Fc, int (&e)[sizeof...(K)],
+                                            std::integer_sequence<int, K...>) {
+  ((e[K] = win_offset<W, M, K>(Fc)), ...);
+}
+
+// One orbit of a window step: the C(W, M) strings sharing the occupation
+// outside the window.  Their addresses are R_O + F[c_lo][S]; every vector of
+// the slab is rotated in registers by the step's Givens rotations.
+template <typename R, int CS, int NST, int W, int M>
+__device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t<R>* const* base,
+                                          size_t st_stride, int chunk, int KV, int kv_eff,
+                                          const WProg<R>& prog, int ga, int gb) {
+  using C = cx_t<R>;
+  constexpr int NS = cbinom(W, M);
+  const int RO = desc & 0xFFFF, clo = (desc >> 16) & 0xFF;
+  const uint16_t* Fc = F + (clo << W);
+  // element offsets (and, in a cluster, the owning CTA) of the orbit
+  int ad[NS];
+  int own[CS > 1 ? NS : 1];
+  win_offsets<W, M>(Fc, ad, std::make_integer_sequence<int, NS>{});
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    int e = RO + ad[k];
+    if constexpr (CS > 1) {
+      int o = 0;
+#pragma unroll
+      for (int r = 1; r < CS; ++r) o += e >= r * chunk;
+      own[k] = o;
+      ad[k] = (e - o * chunk) * KV;
+    } else {
+      ad[k] = e * KV;
+    }
+  }
+  for (int kv = 0; kv < kv_eff; ++kv) {
+    C v[NST][NS];
+#pragma unroll
+    for (int x = 0; x < NST; ++x)
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        v[x][k] = base[CS > 1 ? own[k] : 0][x * st_stride + ad[k] + kv];
+    for (int q = ga; q < gb; ++q) {
+      const R c = prog.c[q], sr = prog.sr[q], si = prog.si[q];
+      switch (prog.u[q]) {
+        case 0: win_pairs<W, M, 0, R, NST, NS>(v, c, sr, si); break;
+        case 1: win_pairs<W, M, 1, R, NST, NS>(v, c, sr, si); break;
+        case 2: win_pairs<W, M, 2, R, NST, NS>(v, c, sr, si); break;
+        case 3: win_pairs<W, M, 3, R, NST, NS>(v, c, sr, si); break;
+        case 4: win_pairs<W, M, 4, R, NST, NS>(v, c, sr, si); break;
+        case 5: win_pairs<W, M, 5, R, NST, NS>(v, c, sr, si); break;
+        case 6: win_pairs<W, M, 6, R, NST, NS>(v, c, sr, si); break;
+        default: break;
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < NST; ++x)
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        base[CS > 1 ? own[k] : 0][x * st_stride + ad[k] + kv] = v[x][k];
+  }
+}
+
+template <typename R, int W, bool WIN>
+struct ProgOf {
+  using type = GProg<R>;
+};
+template <typename R, int W>
+struct ProgOf<R, W, true> {
+  using type = WProg<R>;
 };
 
 // exp(i x) for an FP64 angle: reduced to [-pi, pi] in FP64, then evaluated
@@ -120,9 +277,11 @@ __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
   return reinterpret_cast<const cx_t<R>*>(p)[i];
 }
 
-template <typename R, int CS, int NST, bool VJP>
+// W == 0: one shared-memory pass per Givens rotation (pair lists);
+// W > 0: one pass per window step, orbits rotated in registers.
+template <typename R, int CS, int NST, bool VJP, int W>
 __global__ void __launch_bounds__(kThreads)
-    k_sweep(const SweepGeom g, const __grid_constant__ GProg<R> prog,
+    k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
             const __grid_constant__ Mat X) {
   static_assert(!VJP || NST == 2, "reverse mode carries two states");
   using C = cx_t<R>;
@@ -167,38 +326,61 @@ __global__ void __launch_bounds__(kThreads)
   if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
 
   // ---- Givens rotations, in program order
-  const int items = g.npp << g.lgKV;
-  const int per = (items + CS - 1) / CS;
-  const int lo = rank * per, hi = min(items, lo + per);
-  for (int k = 0; k < prog.m; ++k) {
-    const uint32_t* list = g.pairs + (int64_t)prog.p[k] * g.npp;
-    const R c = prog.c[k], sr = prog.sr[k], si = prog.si[k];
-    for (int it = lo + tid; it < hi; it += kThreads) {
-      int t = it >> g.lgKV, kv = it & (KV - 1);
-      if (kv >= kv_eff) continue;
-      uint32_t pr = __ldg(list + t);
-      int src = pr & 0xFFFF, dst = pr >> 16;
-      int os = 0, od = 0;
-      if constexpr (CS > 1) {
-#pragma unroll
-        for (int r = 1; r < CS; ++r) {
-          os += src >= r * g.chunk;
-          od += dst >= r * g.chunk;
+  if constexpr (W == 0) {
+    const int items = g.npp << g.lgKV;
+    const int per = (items + CS - 1) / CS;
+    const int lo = rank * per, hi = min(items, lo + per);
+    for (int k = 0; k < prog.m; ++k) {
+      const uint32_t* list = g.pairs + (int64_t)prog.p[k] * g.npp;
+      const R c = prog.c[k], sr = prog.sr[k], si = prog.si[k];
+      for (int it = lo + tid; it < hi; it += kThreads) {
+        int t = it >> g.lgKV, kv = it & (KV - 1);
+        if (kv >= kv_eff) continue;
+        uint32_t pr = __ldg(list + t);
+        int src = pr & 0xFFFF, dst = pr >> 16;
+        int os = 0, od = 0;
+        if constexpr (CS > 1) {
+  #pragma unroll
+          for (int r = 1; r < CS; ++r) {
+            os += src >= r * g.chunk;
+            od += dst >= r * g.chunk;
+          }
+        }
+        size_t ls = (size_t)(src - os * g.chunk) * KV + kv;
+        size_t ld = (size_t)(dst - od * g.chunk) * KV + kv;
+  #pragma unroll
+        for (int s = 0; s < NST; ++s) {
+          C* ps = base[os] + s * st_stride + ls;
+          C* pd = base[od] + s * st_stride + ld;
+          C x = *ps, y = *pd;
+          givens2<R>(x, y, c, sr, si);
+          *ps = x;
+          *pd = y;
         }
       }
-      size_t ls = (size_t)(src - os * g.chunk) * KV + kv;
-      size_t ld = (size_t)(dst - od * g.chunk) * KV + kv;
-#pragma unroll
-      for (int s = 0; s < NST; ++s) {
-        C* ps = base[os] + s * st_stride + ls;
-        C* pd = base[od] + s * st_stride + ld;
-        C x = *ps, y = *pd;
-        givens2<R>(x, y, c, sr, si);
-        *ps = x;
-        *pd = y;
-      }
+      if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     }
-    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+  } else {
+    for (int st = 0; st < prog.nsteps; ++st) {
+      const int a = prog.a[st];
+      const int ga = prog.g0[st], gb = prog.g0[st + 1];
+      const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
+      const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
+      const int per = (o1 - o0 + CS - 1) / CS;
+      const int lo = o0 + rank * per, hi = min(o1, lo + per);
+      for (int o = lo + tid; o < hi; o += kThreads) {
+        const uint32_t desc = __ldg(g.orbits + o);
+        switch (desc >> 24) {
+          case 1: win_orbit<R, CS, NST, W, 1>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 2: win_orbit<R, CS, NST, W, 2>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 3: win_orbit<R, CS, NST, W, 3>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 4: if constexpr (W > 4) win_orbit<R, CS, NST, W, 4>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 5: if constexpr (W > 5) win_orbit<R, CS, NST, W, 5>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          default: break;
+        }
+      }
+      if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    }
   }
 
   const int tper = g.nchunk * 256;
@@ -259,29 +441,46 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t* lp = g.xpairs + (int64_t)L * g.nx;
         const uint32_t* ls = g.xsign + (int64_t)L * nw;
         R ar = 0, ai = 0;
-        for (int t = lane; t < cnt; t += 32) {
-          uint32_t pr = __ldg(lp + t);
-          uint32_t sb = (__ldg(ls + (t >> 5)) >> (t & 31)) & 1u;
-          int src = pr & 0xFFFF, dst = pr >> 16;
-          int os = 0, od = 0;
-          if constexpr (CS > 1) {
+        // four list entries per lane in flight: the loads of the pair list
+        // (L2) are independent of the shared-memory arithmetic
+        constexpr int U4 = 4;
+        for (int t0 = 0; t0 < cnt; t0 += 32 * U4) {
+          uint32_t pr[U4], sw[U4];
 #pragma unroll
-            for (int r = 1; r < CS; ++r) {
-              os += src >= r * g.chunk;
-              od += dst >= r * g.chunk;
+          for (int u = 0; u < U4; ++u) {
+            const int t = t0 + u * 32 + lane;
+            pr[u] = t < cnt ? __ldg(lp + t) : 0u;
+            sw[u] = t < cnt ? __ldg(ls + (t >> 5)) : 0u;
+          }
+#pragma unroll
+          for (int u = 0; u < U4; ++u) {
+            const int t = t0 + u * 32 + lane;
+            if (t >= cnt) continue;
+            const uint32_t sb = (sw[u] >> (t & 31)) & 1u;
+            const int src = pr[u] & 0xFFFF, dst = pr[u] >> 16;
+            int os = 0, od = 0;
+            if constexpr (CS > 1) {
+#pragma unroll
+              for (int r = 1; r < CS; ++r) {
+                os += src >= r * g.chunk;
+                od += dst >= r * g.chunk;
+              }
             }
+            const C* ps = base[os] + (size_t)(src - os * g.chunk) * KV;
+            const C* pg = base[od] + st_stride + (size_t)(dst - od * g.chunk) * KV;
+            R br = 0, bi = 0;
+            for (int kv = 0; kv < kv_eff; ++kv) {
+              C a = ps[kv], b = pg[kv];
+              br = fma(b.x, a.x, fma(b.y, a.y, br));
+              bi = fma(b.x, a.y, fma(-b.y, a.x, bi));
+            }
+            if (sb) {
+              br = -br;
+              bi = -bi;
+            }
+            ar += br;
+            ai += bi;
           }
-          const C* ps = base[os] + (size_t)(src - os * g.chunk) * KV;
-          const C* pg = base[od] + st_stride + (size_t)(dst - od * g.chunk) * KV;
-          R br = 0, bi = 0;
-          for (int kv = 0; kv < kv_eff; ++kv) {
-            C a = ps[kv], b = pg[kv];
-            br = fma(b.x, a.x, fma(b.y, a.y, br));
-            bi = fma(b.x, a.y, fma(-b.y, a.x, bi));
-          }
-          if (sb) { br = -br; bi = -bi; }
-          ar += br;
-          ai += bi;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -327,6 +526,46 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Window tables of a space for width W (built once, on the host; see
+// window_tables_host).
+static void build_window_tables(Space* sp, int W) {
+  Space::Win& wt = sp->win[W];
+  if (wt.built) return;
+  std::vector<uint32_t> orbits;
+  std::vector<int> off;
+  std::vector<uint16_t> offs;
+  window_tables_host(sp->norb, sp->nocc, W, orbits, off, offs);
+  FS_CUDA(cudaMalloc(&wt.orbits, std::max<size_t>(orbits.size(), 1) * 4));
+  FS_CUDA(cudaMalloc(&wt.off, off.size() * sizeof(int)));
+  FS_CUDA(cudaMalloc(&wt.offs, offs.size() * 2));
+  if (!orbits.empty())
+    FS_CUDA(cudaMemcpy(wt.orbits, orbits.data(), orbits.size() * 4, cudaMemcpyHostToDevice));
+  FS_CUDA(cudaMemcpy(wt.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  FS_CUDA(cudaMemcpy(wt.offs, offs.data(), offs.size() * 2, cudaMemcpyHostToDevice));
+  wt.built = true;
+}
+
+template <typename R>
+static WProg<R> make_wprog(const RotProgram& rp, int N, int W) {
+  WProg<R> w;
+  std::vector<WinStep> steps = schedule_windows(rp, N, W);
+  int ng = 0;
+  for (size_t st = 0; st < steps.size(); ++st) {
+    w.a[st] = (int8_t)steps[st].a;
+    w.g0[st] = (int16_t)ng;
+    for (int k : steps[st].givens) {
+      w.u[ng] = (int8_t)(rp.g[k].p - steps[st].a);
+      w.c[ng] = (R)rp.g[k].c;
+      w.sr[ng] = (R)rp.g[k].s.real();
+      w.si[ng] = (R)rp.g[k].s.imag();
+      ++ng;
+    }
+  }
+  w.nsteps = (int)steps.size();
+  w.g0[w.nsteps] = (int16_t)ng;
+  return w;
+}
+
 template <typename R>
 static GProg<R> make_prog(const RotProgram& rp) {
   GProg<R> p;
@@ -340,13 +579,13 @@ static GProg<R> make_prog(const RotProgram& rp) {
   return p;
 }
 
-template <typename R, int CS, int NST, bool VJP>
-static void launch_sweep_t(const SweepGeom& g, const GProg<R>& prog, const Mat& X,
+template <typename R, int CS, int NST, bool VJP, int W, typename P>
+static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
                            int nslabs, size_t smem, cudaStream_t st) {
-  auto kern = k_sweep<R, CS, NST, VJP>;
+  auto kern = k_sweep<R, CS, NST, VJP, W>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
-  static const char* names[2][2][2] = {
+  static const char* names[2][2][2] = {  // [f64][reverse][beta]
       {{"sweep_alpha_f32", "sweep_beta_f32"}, {"sweep_vjp_alpha_f32", "sweep_vjp_beta_f32"}},
       {{"sweep_alpha_f64", "sweep_beta_f64"}, {"sweep_vjp_alpha_f64", "sweep_vjp_beta_f64"}}};
   ProfScope ps(names[sizeof(R) == 8][VJP][g.dir], st);
@@ -365,15 +604,42 @@ static void launch_sweep_t(const SweepGeom& g, const GProg<R>& prog, const Mat& 
   FS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, prog, X));
 }
 
-template <typename R, int NST, bool VJP>
-static void dispatch_cs(int CS, const SweepGeom& g, const GProg<R>& prog, const Mat& X,
+template <typename R, int NST, bool VJP, int W, typename P>
+static void dispatch_cs(int CS, const SweepGeom& g, const P& prog, const Mat& X,
                         int nslabs, size_t smem, cudaStream_t st) {
   switch (CS) {
-    case 1: launch_sweep_t<R, 1, NST, VJP>(g, prog, X, nslabs, smem, st); break;
-    case 2: launch_sweep_t<R, 2, NST, VJP>(g, prog, X, nslabs, smem, st); break;
-    case 4: launch_sweep_t<R, 4, NST, VJP>(g, prog, X, nslabs, smem, st); break;
-    case 8: launch_sweep_t<R, 8, NST, VJP>(g, prog, X, nslabs, smem, st); break;
+    case 1: launch_sweep_t<R, 1, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
+    case 2: launch_sweep_t<R, 2, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
+    case 4: launch_sweep_t<R, 4, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
+    case 8: launch_sweep_t<R, 8, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
     default: FS_REQUIRE(false, FS_ERR_UNSUPPORTED, "cluster size out of range");
+  }
+}
+
+// Window width of the register-blocked sweep per precision and state count,
+// chosen so one orbit of every vector fits in registers.
+template <typename R, int NST>
+constexpr int window_width() {
+  return sizeof(R) == 4 ? (NST == 1 ? 6 : 5) : (NST == 1 ? 5 : 4);
+}
+
+template <typename R, int NST, bool VJP>
+static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotProgram& rp,
+                          const Mat& X, int nslabs, size_t smem, cudaStream_t st) {
+  constexpr int W = window_width<R, NST>();
+  if (sthis->norb >= W && sthis->dim > 1) {
+    build_window_tables(sthis, W);
+    SweepGeom g = g0;
+    const Space::Win& wt = sthis->win[W];
+    g.orbits = wt.orbits;
+    g.orb_off = wt.off;
+    g.offs = wt.offs;
+    g.offs_stride = (sthis->nocc + 1) << W;
+    auto prog = make_wprog<R>(rp, sthis->norb, W);
+    dispatch_cs<R, NST, VJP, W>(CS, g, prog, X, nslabs, smem, st);
+  } else {
+    auto prog = make_prog<R>(rp);
+    dispatch_cs<R, NST, VJP, 0>(CS, g0, prog, X, nslabs, smem, st);
   }
 }
 
@@ -432,14 +698,13 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   const int KV = 1 << lg;
   const int nslabs = (g.nvec + KV - 1) / KV;
   const size_t smem = std::max<size_t>(smem_for(CS, KV), 16);
+  Space* sw = const_cast<Space*>(sthis);
   if (dtype == FS_C64) {
-    auto prog = make_prog<float>(rp);
-    if (nst == 1) dispatch_cs<float, 1, false>(CS, g, prog, ph.X, nslabs, smem, st);
-    else dispatch_cs<float, 2, true>(CS, g, prog, ph.X, nslabs, smem, st);
+    if (nst == 1) dispatch_prog<float, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, st);
+    else dispatch_prog<float, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, st);
   } else {
-    auto prog = make_prog<double>(rp);
-    if (nst == 1) dispatch_cs<double, 1, false>(CS, g, prog, ph.X, nslabs, smem, st);
-    else dispatch_cs<double, 2, true>(CS, g, prog, ph.X, nslabs, smem, st);
+    if (nst == 1) dispatch_prog<double, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, st);
+    else dispatch_prog<double, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, st);
   }
 }
 

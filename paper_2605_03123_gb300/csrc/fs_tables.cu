@@ -189,6 +189,11 @@ void free_space(Space* s) {
   cudaFree(s->xpairs);
   cudaFree(s->xsign);
   cudaFree(s->xcount);
+  for (auto& w : s->win) {
+    cudaFree(w.orbits);
+    cudaFree(w.off);
+    cudaFree(w.offs);
+  }
   delete s;
 }
 
