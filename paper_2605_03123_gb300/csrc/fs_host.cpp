@@ -234,3 +234,129 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
 }
 
 }  // namespace fs
+
+namespace fs {
+
+// Subsets of four orbitals covering every unordered orbital pair (greedy:
+// repeatedly the subset covering the most uncovered pairs), each pair and
+// each diagonal assigned to exactly one subset; and, per subset Q, the
+// orbit records of the strings of n electrons: for every configuration O
+// outside Q with m = n - |O| in 1..4, the addresses of O u S for the
+// C(4, m) subsets S of Q (ascending local masks) and the parities of the
+// numbers of O-orbitals in the three gaps of Q.
+void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
+                       std::vector<TRecord>& recs) {
+  passes.clear();
+  recs.clear();
+  if (N < 4) return;
+  std::vector<char> pcov(N * N, 0), dcov(N, 0);
+  int left = N * (N - 1) / 2;
+  while (left > 0) {
+    int best = -1, bq[4] = {0, 1, 2, 3};
+    for (int a = 0; a < N; ++a)
+      for (int b = a + 1; b < N; ++b)
+        for (int c = b + 1; c < N; ++c)
+          for (int d = c + 1; d < N; ++d) {
+            int q[4] = {a, b, c, d}, cnt = 0;
+            for (int i = 0; i < 4; ++i)
+              for (int j = i + 1; j < 4; ++j) cnt += !pcov[q[i] * N + q[j]];
+            if (cnt > best) {
+              best = cnt;
+              for (int i = 0; i < 4; ++i) bq[i] = q[i];
+            }
+          }
+    TPass ps{};
+    for (int i = 0; i < 4; ++i) ps.q[i] = bq[i];
+    ps.keep = 0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int p = bq[i], q = bq[j];
+        bool take = false;
+        if (i == j) {
+          take = !dcov[p];
+          dcov[p] = 1;
+        } else {
+          const int lo = std::min(p, q), hi = std::max(p, q);
+          take = !pcov[lo * N + hi] || (pcov[lo * N + hi] == 2 && i > j);
+        }
+        if (take) ps.keep |= 1u << (i * 4 + j);
+      }
+    // both orders of a newly covered pair belong to this pass
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j) {
+        int k = bq[i] * N + bq[j];
+        if (!pcov[k]) {
+          pcov[k] = 1;
+          --left;
+        }
+      }
+    passes.push_back(ps);
+  }
+  // diagonals of orbitals not yet assigned
+  for (int p = 0; p < N; ++p)
+    if (!dcov[p]) {
+      for (auto& ps : passes)
+        for (int i = 0; i < 4; ++i)
+          if (ps.q[i] == p && !dcov[p]) {
+            ps.keep |= 1u << (i * 5);
+            dcov[p] = 1;
+          }
+    }
+  auto C = [](int a, int b) -> uint64_t {
+    if (b < 0 || b > a) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (uint64_t)(a - b + i) / (uint64_t)i;
+    return r;
+  };
+  auto rank = [&](uint32_t mask) {
+    uint64_t r = 0;
+    int k = 0;
+    for (int o = 0; o < N; ++o)
+      if ((mask >> o) & 1u) r += C(o, ++k);
+    return r;
+  };
+  for (auto& ps : passes) {
+    ps.rec0 = (int)recs.size();
+    uint32_t qmask = 0;
+    for (int i = 0; i < 4; ++i) qmask |= 1u << ps.q[i];
+    std::vector<int> out;
+    for (int p = 0; p < N; ++p)
+      if (!((qmask >> p) & 1u)) out.push_back(p);
+    const int no = (int)out.size();
+    for (int m = 1; m <= 4; ++m) {
+      const int ne = n - m;
+      if (ne < 0 || ne > no) continue;
+      uint64_t x = ne == 0 ? 0 : ((1ull << ne) - 1);
+      while (true) {
+        uint32_t omask = 0;
+        for (int i = 0; i < no; ++i)
+          if ((x >> i) & 1) omask |= 1u << out[i];
+        TRecord r{};
+        int k = 0;
+        for (int s = 0; s < 16; ++s) {
+          if (__builtin_popcount(s) != m) continue;
+          uint32_t full = omask;
+          for (int i = 0; i < 4; ++i)
+            if ((s >> i) & 1) full |= 1u << ps.q[i];
+          r.addr[k++] = (uint16_t)rank(full);
+        }
+        r.m = (uint8_t)m;
+        uint8_t g = 0, acc = 0;
+        for (int j = 0; j < 3; ++j) {
+          uint32_t gap = ((1u << ps.q[j + 1]) - 1u) & ~((2u << ps.q[j]) - 1u);
+          acc ^= (uint8_t)(__builtin_popcount(omask & gap) & 1);
+          g |= (uint8_t)(acc << (j + 1));  // bit j+1: parity of O before q_{j+1}
+        }
+        r.gbits = g;
+        recs.push_back(r);
+        if (ne == 0) break;
+        uint64_t c = x & (~x + 1), rr = x + c;
+        x = (((rr ^ x) >> 2) / c) | rr;
+        if (x >> no) break;
+      }
+    }
+    ps.rec1 = (int)recs.size();
+  }
+}
+
+}  // namespace fs

@@ -60,6 +60,29 @@ std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W);
 void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
                         std::vector<int>& off, std::vector<uint16_t>& offs);
 
+// Device copy of a pass: the subset, the owned slots, the record range.
+struct TPassDev {
+  int q[4];
+  uint32_t keep;
+  int rec0, rec1;
+};
+// Transition-reduction passes (see tpass_tables_host): a subset of four
+// orbitals q[0] < .. < q[3], the local slots (i*4 + j <-> E_{q_i q_j}) this
+// pass owns, and its orbit records recs[rec0 .. rec1) sorted by m.
+struct TPass {
+  int q[4];
+  uint32_t keep;
+  int rec0, rec1;
+};
+struct alignas(16) TRecord {
+  uint16_t addr[6];  // addresses of O u S, S in ascending local-mask order
+  uint8_t m;         // electrons inside the subset
+  uint8_t gbits;     // bit j: parity of |O| between q_0 and q_j (j = 1..3)
+  uint16_t pad;
+};
+void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
+                       std::vector<TRecord>& recs);
+
 // ------------------------------------------------------ device tables
 // Per-sector-spin tables: strings of `nocc` electrons in `norb` orbitals.
 struct Space {
@@ -83,6 +106,11 @@ struct Space {
     uint16_t* offs = nullptr;
     bool built = false;
   } win[8];
+  // transition-reduction passes (reverse mode), built on first use
+  struct TPassDev* tpass = nullptr;
+  struct TRecord* trec = nullptr;
+  int npass = 0;
+  bool tbuilt = false;
 };
 
 struct Scratch {

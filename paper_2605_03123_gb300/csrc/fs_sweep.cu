@@ -74,6 +74,10 @@ struct SweepGeom {
   int nx;
   double* T;  // [norb][norb] complex accumulator: += <g| E_pq |psi>
   void* W;    // [d_a][d_b] real: Im(conj(g) psi), or null
+  // transition-reduction passes of the rotated spin (reverse mode, N >= 4)
+  const TPassDev* tpass;
+  const TRecord* trec;
+  int npass;
   // window tables of the rotated spin (window kernels only)
   const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
   const int* orb_off;      // [npos + 1] start of each position's list
@@ -206,6 +210,117 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
       for (int k = 0; k < NS; ++k)
         base[CS > 1 ? own[k] : 0][x * st_stride + ad[k] + kv] = v[x][k];
   }
+}
+
+// ------------------------------------------------ transition reduction
+// One orbit of a transition pass: the C(4, M) strings O u S for the
+// subset Q = {q_0 < .. < q_3}.  For every local pair (a, b) with b in S and
+// a not in S, a^dag_{q_a} a_{q_b} maps S to S' = S - b + a with the sign
+// (-1)^(#occupied orbitals strictly between q_a and q_b): the part inside Q
+// is a compile-time constant, the part from O is folded into the loaded
+// amplitudes (omega(S) = prod over j in S of (-1)^{G_j}, G_j the parity of
+// O between q_0 and q_j, so omega(S) omega(S') is the O parity of the pair).
+// acc[2 (a*4 + b)], acc[2 (a*4 + b) + 1] += Re, Im of conj(g[S']) psi[S].
+template <typename R, int M, int J, int NS>
+__device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
+                                       R (&acc)[32]) {
+  constexpr int k = J / 16, a = (J / 4) % 4, b = J % 4;
+  if constexpr (k < NS) {
+    constexpr int S = win_mask(4, M, k);
+    if constexpr ((S >> b) & 1) {
+      if constexpr (a == b) {
+        acc[2 * (a * 4 + b)] += pg[k].x * ps[k].x + pg[k].y * ps[k].y;
+        acc[2 * (a * 4 + b) + 1] += pg[k].x * ps[k].y - pg[k].y * ps[k].x;
+      } else if constexpr (!((S >> a) & 1)) {
+        constexpr int k2 = win_index(4, M, S ^ (1 << a) ^ (1 << b));
+        constexpr int lo = a < b ? a : b, hi = a < b ? b : a;
+        constexpr bool neg = cpopc(S & ((1 << hi) - 1) & ~((2 << lo) - 1)) & 1;
+        const R re = fma(pg[k2].x, ps[k].x, pg[k2].y * ps[k].y);
+        const R im = fma(pg[k2].x, ps[k].y, -pg[k2].y * ps[k].x);
+        if constexpr (neg) {
+          acc[2 * (a * 4 + b)] -= re;
+          acc[2 * (a * 4 + b) + 1] -= im;
+        } else {
+          acc[2 * (a * 4 + b)] += re;
+          acc[2 * (a * 4 + b) + 1] += im;
+        }
+      }
+    }
+  }
+}
+template <typename R, int M, int NS, int... J>
+__device__ __forceinline__ void t_terms(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
+                                        R (&acc)[32], std::integer_sequence<int, J...>) {
+  (t_term<R, M, J, NS>(ps, pg, acc), ...);
+}
+template <int M, int K>
+__device__ __forceinline__ int t_flip(int gb) {
+  constexpr int S = win_mask(4, M, K);
+  int f = 0;
+#pragma unroll
+  for (int j = 1; j < 4; ++j)
+    if ((S >> j) & 1) f ^= (gb >> j) & 1;
+  return f;
+}
+template <int M, int... K>
+__device__ __forceinline__ void t_flips(int gb, int (&fl)[sizeof...(K)],
+                                        std::integer_sequence<int, K...>) {
+  ((fl[K] = t_flip<M, K>(gb)), ...);
+}
+template <typename R, int CS, int M>
+__device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base, size_t st_stride,
+                                        int chunk, int KV, int kv_eff, R (&acc)[32]) {
+  using C = cx_t<R>;
+  constexpr int NS = cbinom(4, M);
+  int ad[NS], own[CS > 1 ? NS : 1];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int e = rc.addr[k];
+    if constexpr (CS > 1) {
+      int o = 0;
+#pragma unroll
+      for (int r = 1; r < CS; ++r) o += e >= r * chunk;
+      own[k] = o;
+      ad[k] = (e - o * chunk) * KV;
+    } else {
+      ad[k] = e * KV;
+    }
+  }
+  int fl[NS];
+  t_flips<M>(rc.gbits, fl, std::make_integer_sequence<int, NS>{});
+  for (int kv = 0; kv < kv_eff; ++kv) {
+    C ps[NS], pg[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      C* b0 = base[CS > 1 ? own[k] : 0];
+      ps[k] = b0[ad[k] + kv];
+      pg[k] = b0[st_stride + ad[k] + kv];
+      if (fl[k]) {
+        ps[k].x = -ps[k].x;
+        ps[k].y = -ps[k].y;
+        pg[k].x = -pg[k].x;
+        pg[k].y = -pg[k].y;
+      }
+    }
+    t_terms<R, M, NS>(ps, pg, acc, std::make_integer_sequence<int, 6 * 16>{});
+  }
+}
+
+// Warp reduction of 32 values by recursive halving: afterwards lane l holds
+// the sum over the warp of value l.
+template <typename R>
+__device__ __forceinline__ R warp_transpose_sum(R (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const bool up = lane & s;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const R send = up ? v[i] : v[i + s];
+      const R keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, s);
+    }
+  }
+  return v[0];
 }
 
 template <typename R, int W, bool WIN>
@@ -431,7 +546,43 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     // (b) T[p][q] += sum over the slab of sign * conj(g[dst]) * psi[src] for
     //     every pair (src, dst = src^{q->p}) of the E_pq list of this spin
-    if (g.T) {
+    if (g.T && g.npass > 0) {
+      // subset passes: per-thread partial sums of the 16 local slots, one
+      // warp reduction per pass, per-CTA sums in shared memory
+      R* tsm = reinterpret_cast<R*>(w + (g.has_x ? (kMaxOrb << g.lgKV) : 0));
+      for (int i = tid; i < g.npass * 32; i += kThreads) tsm[i] = 0;
+      __syncthreads();
+      const int lane = tid & 31;
+      for (int P = 0; P < g.npass; ++P) {
+        const TPassDev pd = g.tpass[P];
+        R acc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0;
+        const int per = (pd.rec1 - pd.rec0 + CS - 1) / CS;
+        const int lo = pd.rec0 + rank * per, hi = min(pd.rec1, lo + per);
+        for (int o = lo + tid; o < hi; o += kThreads) {
+          TRecord rc;
+          *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
+          switch (rc.m) {
+            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
+            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
+            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
+            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
+            default: break;
+          }
+        }
+        const R v = warp_transpose_sum<R>(acc, lane);
+        if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + P * 32 + lane, v);
+      }
+      __syncthreads();
+      for (int i = tid; i < g.npass * 32; i += kThreads) {
+        const TPassDev pd = g.tpass[i >> 5];
+        const int slot = (i & 31) >> 1;
+        if (!(pd.keep & (1u << slot))) continue;
+        const int p = pd.q[slot >> 2], q = pd.q[slot & 3];
+        atomicAdd(g.T + 2 * (p * g.norb + q) + (i & 1), (double)tsm[i]);
+      }
+    } else if (g.T) {
       const int lane = tid & 31;
       const int nw = (g.nx + 31) / 32;
       const int gw = rank * (kThreads / 32) + (tid >> 5);
@@ -524,6 +675,33 @@ __global__ void __launch_bounds__(kThreads)
     // remote CTAs may still read this CTA's shared memory in (b)
     if constexpr (CS > 1) cg::this_cluster().sync();
   }
+}
+
+// Transition-reduction passes of a space (built once, on the host; see
+// tpass_tables_host).
+static void build_tpass_tables(Space* sp) {
+  if (sp->tbuilt) return;
+  std::vector<TPass> passes;
+  std::vector<TRecord> recs;
+  tpass_tables_host(sp->norb, sp->nocc, passes, recs);
+  std::vector<TPassDev> pd(passes.size());
+  for (size_t i = 0; i < passes.size(); ++i) {
+    for (int j = 0; j < 4; ++j) pd[i].q[j] = passes[i].q[j];
+    pd[i].keep = passes[i].keep;
+    pd[i].rec0 = passes[i].rec0;
+    pd[i].rec1 = passes[i].rec1;
+  }
+  if (!pd.empty()) {
+    FS_CUDA(cudaMalloc(&sp->tpass, pd.size() * sizeof(TPassDev)));
+    FS_CUDA(cudaMemcpy(sp->tpass, pd.data(), pd.size() * sizeof(TPassDev),
+                       cudaMemcpyHostToDevice));
+    FS_CUDA(cudaMalloc(&sp->trec, std::max<size_t>(recs.size(), 1) * sizeof(TRecord)));
+    if (!recs.empty())
+      FS_CUDA(cudaMemcpy(sp->trec, recs.data(), recs.size() * sizeof(TRecord),
+                         cudaMemcpyHostToDevice));
+  }
+  sp->npass = (int)pd.size();
+  sp->tbuilt = true;
 }
 
 // Window tables of a space for width W (built once, on the host; see
@@ -677,14 +855,21 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
     g.nx = sthis->nx;
     g.T = sthis->nx > 0 ? rev->T : nullptr;
     g.W = rev->W;
+    if (g.T && sthis->norb >= 4 && sthis->nocc >= 1) {
+      build_tpass_tables(const_cast<Space*>(sthis));
+      g.tpass = sthis->tpass;
+      g.trec = sthis->trec;
+      g.npass = sthis->npass;
+    }
   }
   const size_t csz = dtype == FS_C64 ? 8 : 16;
   const size_t maxsm = (size_t)ctx->prop.sharedMemPerBlockOptin;
   const size_t tab_per_kv = ph.has_x ? g.nchunk * 256 * csz : 0;
   const size_t fixed = ph.has_x ? kMaxOrb * sizeof(double) : 0;
+  const size_t tsum = (size_t)g.npass * 32 * (csz / 2);  // per-CTA pass sums
   auto smem_for = [&](int CS, int KV) {
     size_t chunk = (g.d + CS - 1) / CS;
-    return (size_t)KV * (chunk * csz * nst + tab_per_kv + fixed);
+    return (size_t)KV * (chunk * csz * nst + tab_per_kv + fixed) + tsum;
   };
   int CS = 1;
   while (CS <= 8 && smem_for(CS, 1) > maxsm) CS *= 2;

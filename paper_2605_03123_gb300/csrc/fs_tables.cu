@@ -189,6 +189,8 @@ void free_space(Space* s) {
   cudaFree(s->xpairs);
   cudaFree(s->xsign);
   cudaFree(s->xcount);
+  cudaFree(s->tpass);
+  cudaFree(s->trec);
   for (auto& w : s->win) {
     cudaFree(w.orbits);
     cudaFree(w.off);
