@@ -90,7 +90,13 @@ int fs_sync_status(fs_ctx *ctx, void *stream);
 int fs_profile_start(fs_ctx *ctx);
 int fs_profile_stop(fs_ctx *ctx, char *out, int64_t cap);
 
-/* Force or release the orbital-rotation method (default FS_ROT_AUTO). */
+/* Force or release the orbital-rotation method (default FS_ROT_AUTO).
+ * Under FS_ROT_AUTO the first fs_apply_orbital_rotation call for a sector
+ * and dtype whose string dimensions allow the minor-matrix method (both at
+ * most 4096) times both methods on a scratch copy of the state, which
+ * synchronizes the stream once, and the faster method is used from then on
+ * for that sector and dtype.  FS_ROT_MINORS on a larger sector returns
+ * FS_ERR_UNSUPPORTED. */
 int fs_set_rotation_path(fs_ctx *ctx, int path);
 
 /* Sector string tables, built on the device with the combinatorial number

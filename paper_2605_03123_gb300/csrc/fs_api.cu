@@ -157,6 +157,61 @@ static void phase_pass(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
   launch_phase(sa, sb, vec, dtype, ph, st);
 }
 
+static CMat cmat_of(const std::vector<zd>& U, int n) {
+  CMat m{};
+  for (int k = 0; k < n * n; ++k) {
+    m.v[2 * k] = U[k].real();
+    m.v[2 * k + 1] = U[k].imag();
+  }
+  return m;
+}
+
+// Orbital rotation by the selected method.  FS_ROT_AUTO measures both
+// methods once per (sector, dtype) on a scratch copy of the state (the
+// first such call synchronizes the stream) and keeps the faster.
+static void rotate_any(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
+                       const std::vector<zd>& Ua, const std::vector<zd>& Ub,
+                       const RotProgram& pa, const RotProgram& pb, cudaStream_t st) {
+  const int n = sa->norb;
+  int path = ctx->rot_path;
+  if (path == FS_ROT_AUTO) {
+    if (!minor_path_supported(sa, sb)) {
+      path = FS_ROT_GIVENS;
+    } else {
+      auto key = std::make_tuple(n, sa->nocc, sb->nocc, dtype);
+      auto it = ctx->rot_choice.find(key);
+      if (it != ctx->rot_choice.end()) {
+        path = it->second;
+      } else {
+        const size_t bytes = sa->dim * sb->dim * (dtype == FS_C64 ? 8 : 16);
+        void* tv = scratch(ctx, "autotune_state", bytes);
+        FS_CUDA(cudaMemcpyAsync(tv, vec, bytes, cudaMemcpyDeviceToDevice, st));
+        cudaEvent_t e[3];
+        for (auto& x : e) FS_CUDA(cudaEventCreate(&x));
+        float tg = 0, tm = 0;
+        for (int rep = 0; rep < 2; ++rep) {  // first round warms up
+          FS_CUDA(cudaEventRecord(e[0], st));
+          for (int k = 0; k < 3; ++k) rotate(ctx, sa, sb, tv, nullptr, 1, dtype, pa, pb, nullptr, st);
+          FS_CUDA(cudaEventRecord(e[1], st));
+          for (int k = 0; k < 3; ++k)
+            launch_minor_rotation(ctx, sa, sb, tv, dtype, cmat_of(Ua, n), cmat_of(Ub, n), st);
+          FS_CUDA(cudaEventRecord(e[2], st));
+          FS_CUDA(cudaEventSynchronize(e[2]));
+          FS_CUDA(cudaEventElapsedTime(&tg, e[0], e[1]));
+          FS_CUDA(cudaEventElapsedTime(&tm, e[1], e[2]));
+        }
+        for (auto& x : e) cudaEventDestroy(x);
+        path = tm < tg ? FS_ROT_MINORS : FS_ROT_GIVENS;
+        ctx->rot_choice[key] = path;
+      }
+    }
+  }
+  if (path == FS_ROT_MINORS)
+    launch_minor_rotation(ctx, sa, sb, vec, dtype, cmat_of(Ua, n), cmat_of(Ub, n), st);
+  else
+    rotate(ctx, sa, sb, vec, nullptr, 1, dtype, pa, pb, nullptr, st);
+}
+
 template <class F>
 static int guarded(F&& f) {
   try {
@@ -361,7 +416,7 @@ int fs_apply_orbital_rotation(fs_ctx* ctx, void* vec, int dtype, const double* U
     Space* sb = get_space(ctx, norb, nb, st);
     RotProgram pa = decompose_adjacent(norb, Ua.data());
     RotProgram pb = U_b ? decompose_adjacent(norb, Ub.data()) : pa;
-    rotate(ctx, sa, sb, vec, nullptr, 1, dtype, pa, pb, nullptr, st);
+    rotate_any(ctx, sa, sb, vec, dtype, Ua, Ub, pa, pb, st);
   });
 }
 

@@ -2,6 +2,7 @@
 // of its Frechet derivative, unitarity checks, and the adjacent-pair Givens
 // decomposition of an orbital-rotation matrix (§3.2.3).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 
@@ -249,47 +250,84 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
   passes.clear();
   recs.clear();
   if (N < 4) return;
-  std::vector<char> pcov(N * N, 0), dcov(N, 0);
-  int left = N * (N - 1) / 2;
-  while (left > 0) {
-    int best = -1, bq[4] = {0, 1, 2, 3};
+  // N = 16: the lines of the affine plane over GF(4), 20 subsets covering
+  // every pair exactly once (point (x, y) <-> orbital 4x + y; GF(4) addition
+  // is XOR of 2-bit codes, multiplication by the table below).
+  // Otherwise: greedy covering, best of several seeded randomized tie-breaks.
+  std::vector<std::array<int, 4>> cover;
+  if (N == 16) {
+    static const int mul[4][4] = {{0, 0, 0, 0}, {0, 1, 2, 3}, {0, 2, 3, 1}, {0, 3, 1, 2}};
+    for (int m = 0; m < 4; ++m)
+      for (int b = 0; b < 4; ++b) {
+        std::array<int, 4> q;
+        for (int x = 0; x < 4; ++x) q[x] = 4 * x + (mul[m][x] ^ b);
+        std::sort(q.begin(), q.end());
+        cover.push_back(q);
+      }
+    for (int c = 0; c < 4; ++c) cover.push_back({4 * c, 4 * c + 1, 4 * c + 2, 4 * c + 3});
+  } else {
+    std::vector<std::array<int, 4>> all;
     for (int a = 0; a < N; ++a)
       for (int b = a + 1; b < N; ++b)
         for (int c = b + 1; c < N; ++c)
-          for (int d = c + 1; d < N; ++d) {
-            int q[4] = {a, b, c, d}, cnt = 0;
-            for (int i = 0; i < 4; ++i)
-              for (int j = i + 1; j < 4; ++j) cnt += !pcov[q[i] * N + q[j]];
-            if (cnt > best) {
-              best = cnt;
-              for (int i = 0; i < 4; ++i) bq[i] = q[i];
-            }
+          for (int d = c + 1; d < N; ++d) all.push_back({a, b, c, d});
+    uint64_t rng = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+      rng ^= rng << 13;
+      rng ^= rng >> 7;
+      rng ^= rng << 17;
+      return rng;
+    };
+    const int tries = N <= 20 ? 64 : 4;
+    for (int t = 0; t < tries; ++t) {
+      std::vector<char> cov(N * N, 0);
+      std::vector<std::array<int, 4>> cur;
+      int left = N * (N - 1) / 2;
+      while (left > 0) {
+        int best = -1;
+        std::vector<int> ties;
+        for (size_t i = 0; i < all.size(); ++i) {
+          const auto& q = all[i];
+          int cnt = 0;
+          for (int x = 0; x < 4; ++x)
+            for (int y = x + 1; y < 4; ++y) cnt += !cov[q[x] * N + q[y]];
+          if (cnt > best) {
+            best = cnt;
+            ties.clear();
           }
+          if (cnt == best) ties.push_back((int)i);
+        }
+        const auto& q = all[ties[t == 0 ? 0 : next() % ties.size()]];
+        for (int x = 0; x < 4; ++x)
+          for (int y = x + 1; y < 4; ++y)
+            if (!cov[q[x] * N + q[y]]) {
+              cov[q[x] * N + q[y]] = 1;
+              --left;
+            }
+        cur.push_back(q);
+      }
+      if (cover.empty() || cur.size() < cover.size()) cover = cur;
+    }
+  }
+  std::vector<char> pcov(N * N, 0), dcov(N, 0);
+  for (const auto& bq : cover) {
     TPass ps{};
     for (int i = 0; i < 4; ++i) ps.q[i] = bq[i];
     ps.keep = 0;
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) {
         const int p = bq[i], q = bq[j];
-        bool take = false;
+        bool take;
         if (i == j) {
           take = !dcov[p];
           dcov[p] = 1;
         } else {
-          const int lo = std::min(p, q), hi = std::max(p, q);
-          take = !pcov[lo * N + hi] || (pcov[lo * N + hi] == 2 && i > j);
+          take = !pcov[std::min(p, q) * N + std::max(p, q)];
         }
         if (take) ps.keep |= 1u << (i * 4 + j);
       }
-    // both orders of a newly covered pair belong to this pass
     for (int i = 0; i < 4; ++i)
-      for (int j = i + 1; j < 4; ++j) {
-        int k = bq[i] * N + bq[j];
-        if (!pcov[k]) {
-          pcov[k] = 1;
-          --left;
-        }
-      }
+      for (int j = i + 1; j < 4; ++j) pcov[bq[i] * N + bq[j]] = 1;
     passes.push_back(ps);
   }
   // diagonals of orbitals not yet assigned

@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -23,6 +24,8 @@ constexpr int kMaxOrb = kMaxNorb;
 constexpr int kMaxGivens = kMaxNorb * (kMaxNorb - 1) / 2;
 // Vector length limit of the sweep kernels (16-bit addresses in pair lists).
 constexpr int64_t kMaxSweepDim = 65535;
+// String-dimension limit of the dense minor-matrix rotation.
+constexpr int64_t kMaxMinorDim = 4096;
 
 // ------------------------------------------------------------- host math
 // One adjacent-pair Givens rotation G = [[c, s], [-s*, c]] on orbitals
@@ -126,6 +129,8 @@ struct ProfRec {
 
 struct Ctx {
   int device = 0;
+  // autotuned orbital-rotation method per (norb, n_alpha, n_beta, dtype)
+  std::map<std::tuple<int, int, int, int>, int> rot_choice;
   bool prof_on = false;
   std::vector<ProfRec> prof;
   cudaDeviceProp prop{};
@@ -245,6 +250,12 @@ void launch_slater(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dt
                    const CMat& R, cudaStream_t st);
 
 void launch_exc_table(const Space* sp, uint32_t* out, cudaStream_t st);
+
+// Dense minor-matrix rotation psi <- M_a psi M_b^T (§2.3), U_a and U_b by
+// value.  Supported for string dimensions up to kMaxMinorDim.
+bool minor_path_supported(const Space* sa, const Space* sb);
+void launch_minor_rotation(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dtype,
+                           const CMat& Ua, const CMat& Ub, cudaStream_t st);
 // masks[dim] of the strings of nocc electrons in norb orbitals, into `out`.
 void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st);
 

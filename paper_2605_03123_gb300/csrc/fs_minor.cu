@@ -1,0 +1,177 @@
+// Orbital rotation by dense minor matrices, for small string dimensions.
+//
+// From U a^dag_p U^dag = sum_q U_qp a^dag_q (§2.3) applied to every creation
+// operator of |I> = cre(I)|vac>, the rotated string is
+//   U|I> = sum_J det(U[J, I]) |J>   (rows J, columns I, both ascending),
+// so one spin is rotated by the matrix M[J][I] = det(U[J, I]) and the state
+// by psi' = M_a psi M_b^T.  The minors are computed in FP64 on the device,
+// then the two products run as tiled complex GEMMs in the state precision.
+#include <algorithm>
+
+#include "fs_common.cuh"
+#include "fs_internal.h"
+
+namespace fs {
+
+constexpr int kMinorMaxN = 16;  // electrons per spin on this path
+
+// M[J][I] = det(U[rows of J, columns of I]), FP64 Gaussian elimination with
+// partial pivoting; one thread per entry.
+template <typename R>
+__global__ void k_minor_matrix(cx_t<R>* M, const uint32_t* masks, int64_t d, int norb, int n,
+                               const __grid_constant__ CMat U) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= d * d) return;
+  const int64_t J = t / d, I = t - J * d;
+  double2 a[kMinorMaxN * kMinorMaxN];
+  const uint32_t mj = masks[J], mi = masks[I];
+  int r = 0;
+  for (int p = 0; p < norb; ++p) {
+    if (!((mj >> p) & 1u)) continue;
+    int c = 0;
+    for (int q = 0; q < norb; ++q) {
+      if (!((mi >> q) & 1u)) continue;
+      a[r * n + c] = make_double2(U.v[2 * (p * norb + q)], U.v[2 * (p * norb + q) + 1]);
+      ++c;
+    }
+    ++r;
+  }
+  double dr = 1, di = 0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = hypot(a[k * n + k].x, a[k * n + k].y);
+    for (int i = k + 1; i < n; ++i) {
+      double h = hypot(a[i * n + k].x, a[i * n + k].y);
+      if (h > best) {
+        best = h;
+        piv = i;
+      }
+    }
+    if (best == 0) {
+      dr = di = 0;
+      break;
+    }
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) {
+        double2 tmp = a[k * n + c];
+        a[k * n + c] = a[piv * n + c];
+        a[piv * n + c] = tmp;
+      }
+      dr = -dr;
+      di = -di;
+    }
+    const double2 pk = a[k * n + k];
+    const double nr = dr * pk.x - di * pk.y;
+    di = dr * pk.y + di * pk.x;
+    dr = nr;
+    const double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
+    for (int i = k + 1; i < n; ++i) {
+      const double2 x = a[i * n + k];
+      const double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
+      for (int c = k + 1; c < n; ++c) {
+        const double2 y = a[k * n + c];
+        a[i * n + c].x -= fr * y.x - fi * y.y;
+        a[i * n + c].y -= fr * y.y + fi * y.x;
+      }
+    }
+  }
+  M[t] = mk<R>((R)dr, (R)di);
+}
+
+// C[m][n] = sum_k A[m][k] * B'[k][n] with B' = B (TB = false) or B^T
+// (TB = true, B stored [n][k]); complex, 64 x 64 tiles, 256 threads, each
+// thread 4 x 4 outputs.
+constexpr int kTile = 64, kTk = 16;
+template <typename R, bool TB>
+__global__ void __launch_bounds__(256)
+    k_cgemm(const cx_t<R>* A, const cx_t<R>* B, cx_t<R>* Cm, int M, int N, int K) {
+  using Cx = cx_t<R>;
+  __shared__ Cx sa[kTk][kTile + 1];
+  __shared__ Cx sb[kTk][kTile + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+  Cx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += kTk) {
+    for (int e = threadIdx.x; e < kTk * kTile; e += 256) {
+      const int kk = e / kTile, mm = e - kk * kTile;
+      const int gm = m0 + mm, gk = k0 + kk;
+      sa[kk][mm] = (gm < M && gk < K) ? A[(int64_t)gm * K + gk] : mk<R>(0, 0);
+      const int gn = n0 + mm;
+      Cx bv = mk<R>(0, 0);
+      if (gn < N && gk < K) bv = TB ? B[(int64_t)gn * K + gk] : B[(int64_t)gk * N + gn];
+      sb[kk][mm] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTk; ++kk) {
+      Cx av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sa[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = sb[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(av[i].x, bv[j].x, fma(-av[i].y, bv[j].y, acc[i][j].x));
+          acc[i][j].y = fma(av[i].x, bv[j].y, fma(av[i].y, bv[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+      if (gm < M && gn < N) Cm[(int64_t)gm * N + gn] = acc[i][j];
+    }
+}
+
+template <typename R>
+static void minor_rotation_t(Ctx* ctx, const Space* sa, const Space* sb, void* vec,
+                             const CMat& Ua, const CMat& Ub, cudaStream_t st) {
+  using Cx = cx_t<R>;
+  const int64_t da = sa->dim, db = sb->dim;
+  Cx* Ma = (Cx*)scratch(ctx, "minor_a", da * da * sizeof(Cx));
+  Cx* Mb = (Cx*)scratch(ctx, "minor_b", db * db * sizeof(Cx));
+  Cx* tmp = (Cx*)scratch(ctx, "minor_tmp", da * db * sizeof(Cx));
+  {
+    ProfScope ps("minor_matrices", st, 2);
+    k_minor_matrix<R><<<(unsigned)((da * da + 127) / 128), 128, 0, st>>>(Ma, sa->masks, da,
+                                                                          sa->norb, sa->nocc, Ua);
+    FS_CUDA(cudaGetLastError());
+    k_minor_matrix<R><<<(unsigned)((db * db + 127) / 128), 128, 0, st>>>(Mb, sb->masks, db,
+                                                                          sb->norb, sb->nocc, Ub);
+    FS_CUDA(cudaGetLastError());
+  }
+  ProfScope ps(sizeof(R) == 4 ? "minor_gemm_f32" : "minor_gemm_f64", st, 2);
+  // tmp = psi M_b^T, then psi = M_a tmp
+  dim3 g1((unsigned)((db + kTile - 1) / kTile), (unsigned)((da + kTile - 1) / kTile));
+  k_cgemm<R, true><<<g1, 256, 0, st>>>((const Cx*)vec, Mb, tmp, (int)da, (int)db, (int)db);
+  FS_CUDA(cudaGetLastError());
+  k_cgemm<R, false><<<g1, 256, 0, st>>>(Ma, tmp, (Cx*)vec, (int)da, (int)db, (int)da);
+  FS_CUDA(cudaGetLastError());
+}
+
+bool minor_path_supported(const Space* sa, const Space* sb) {
+  return sa->dim <= kMaxMinorDim && sb->dim <= kMaxMinorDim && sa->nocc <= kMinorMaxN &&
+         sb->nocc <= kMinorMaxN;
+}
+
+void launch_minor_rotation(Ctx* ctx, const Space* sa, const Space* sb, void* vec, int dtype,
+                           const CMat& Ua, const CMat& Ub, cudaStream_t st) {
+  FS_REQUIRE(minor_path_supported(sa, sb), FS_ERR_UNSUPPORTED,
+             "the minor-matrix rotation supports string dimensions up to 4096 and at most "
+             "16 electrons per spin");
+  if (dtype == FS_C64)
+    minor_rotation_t<float>(ctx, sa, sb, vec, Ua, Ub, st);
+  else
+    minor_rotation_t<double>(ctx, sa, sb, vec, Ua, Ub, st);
+}
+
+}  // namespace fs

@@ -22,7 +22,6 @@ namespace cg = cooperative_groups;
 
 namespace fs {
 
-constexpr int kThreads = 512;
 constexpr int kMaxKV = 64;
 
 template <typename R>
@@ -223,26 +222,27 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
 // acc[2 (a*4 + b)], acc[2 (a*4 + b) + 1] += Re, Im of conj(g[S']) psi[S].
 template <typename R, int M, int J, int NS>
 __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
-                                       R (&acc)[32]) {
+                                       R (&acc)[32], uint32_t keep) {
   constexpr int k = J / 16, a = (J / 4) % 4, b = J % 4;
   if constexpr (k < NS) {
     constexpr int S = win_mask(4, M, k);
+    constexpr int slot = a * 4 + b;
     if constexpr ((S >> b) & 1) {
       if constexpr (a == b) {
-        acc[2 * (a * 4 + b)] += pg[k].x * ps[k].x + pg[k].y * ps[k].y;
-        acc[2 * (a * 4 + b) + 1] += pg[k].x * ps[k].y - pg[k].y * ps[k].x;
+        if (keep & (1u << slot)) {  // uniform per pass: diagonals are owned once
+          acc[2 * slot] = fma(pg[k].x, ps[k].x, fma(pg[k].y, ps[k].y, acc[2 * slot]));
+          acc[2 * slot + 1] = fma(pg[k].x, ps[k].y, fma(-pg[k].y, ps[k].x, acc[2 * slot + 1]));
+        }
       } else if constexpr (!((S >> a) & 1)) {
         constexpr int k2 = win_index(4, M, S ^ (1 << a) ^ (1 << b));
         constexpr int lo = a < b ? a : b, hi = a < b ? b : a;
         constexpr bool neg = cpopc(S & ((1 << hi) - 1) & ~((2 << lo) - 1)) & 1;
-        const R re = fma(pg[k2].x, ps[k].x, pg[k2].y * ps[k].y);
-        const R im = fma(pg[k2].x, ps[k].y, -pg[k2].y * ps[k].x);
-        if constexpr (neg) {
-          acc[2 * (a * 4 + b)] -= re;
-          acc[2 * (a * 4 + b) + 1] -= im;
-        } else {
-          acc[2 * (a * 4 + b)] += re;
-          acc[2 * (a * 4 + b) + 1] += im;
+        constexpr R sg = neg ? R(-1) : R(1);
+        if (keep & (1u << slot)) {  // uniform per pass: each pair is owned once
+          // acc += sg * conj(g[k2]) * psi[k], as four fused multiply-adds
+          const R gx = sg * pg[k2].x, gy = sg * pg[k2].y;
+          acc[2 * slot] = fma(gx, ps[k].x, fma(gy, ps[k].y, acc[2 * slot]));
+          acc[2 * slot + 1] = fma(gx, ps[k].y, fma(-gy, ps[k].x, acc[2 * slot + 1]));
         }
       }
     }
@@ -250,8 +250,9 @@ __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&
 }
 template <typename R, int M, int NS, int... J>
 __device__ __forceinline__ void t_terms(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
-                                        R (&acc)[32], std::integer_sequence<int, J...>) {
-  (t_term<R, M, J, NS>(ps, pg, acc), ...);
+                                        R (&acc)[32], uint32_t keep,
+                                        std::integer_sequence<int, J...>) {
+  (t_term<R, M, J, NS>(ps, pg, acc, keep), ...);
 }
 template <int M, int K>
 __device__ __forceinline__ int t_flip(int gb) {
@@ -269,7 +270,8 @@ __device__ __forceinline__ void t_flips(int gb, int (&fl)[sizeof...(K)],
 }
 template <typename R, int CS, int M>
 __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base, size_t st_stride,
-                                        int chunk, int KV, int kv_eff, R (&acc)[32]) {
+                                        int chunk, int KV, int kv_eff, R (&acc)[32],
+                                        uint32_t keep) {
   using C = cx_t<R>;
   constexpr int NS = cbinom(4, M);
   int ad[NS], own[CS > 1 ? NS : 1];
@@ -302,7 +304,7 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
         pg[k].y = -pg[k].y;
       }
     }
-    t_terms<R, M, NS>(ps, pg, acc, std::make_integer_sequence<int, 6 * 16>{});
+    t_terms<R, M, NS>(ps, pg, acc, keep, std::make_integer_sequence<int, 6 * 16>{});
   }
 }
 
@@ -394,11 +396,16 @@ __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
 
 // W == 0: one shared-memory pass per Givens rotation (pair lists);
 // W > 0: one pass per window step, orbits rotated in registers.
-template <typename R, int CS, int NST, bool VJP, int W>
-__global__ void __launch_bounds__(kThreads)
+// NT threads per CTA.  SPLIT (two states, no cluster): during the Givens
+// phase the first half of the CTA rotates state 0 and the second half state
+// 1, each half synchronising on its own named barrier.
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
             const __grid_constant__ Mat X) {
   static_assert(!VJP || NST == 2, "reverse mode carries two states");
+  static_assert(!SPLIT || (NST == 2 && CS == 1 && W > 0), "split mode: two states, one CTA");
+  constexpr int kThreads = NT;
   using C = cx_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -475,6 +482,30 @@ __global__ void __launch_bounds__(kThreads)
       }
       if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     }
+  } else if constexpr (SPLIT) {
+    // half h rotates state h; its threads meet on named barrier 1 + h
+    constexpr int HT = NT / 2;
+    const int half = tid / HT, ltid = tid - half * HT;
+    C* bs[1] = {sm + half * st_stride};
+    for (int st = 0; st < prog.nsteps; ++st) {
+      const int a = prog.a[st];
+      const int ga = prog.g0[st], gb = prog.g0[st + 1];
+      const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
+      const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
+      for (int o = o0 + ltid; o < o1; o += HT) {
+        const uint32_t desc = __ldg(g.orbits + o);
+        switch (desc >> 24) {
+          case 1: win_orbit<R, 1, 1, W, 1>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 2: win_orbit<R, 1, 1, W, 2>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 3: win_orbit<R, 1, 1, W, 3>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 4: if constexpr (W > 4) win_orbit<R, 1, 1, W, 4>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 5: if constexpr (W > 5) win_orbit<R, 1, 1, W, 5>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          default: break;
+        }
+      }
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(HT) : "memory");
+    }
+    __syncthreads();
   } else {
     for (int st = 0; st < prog.nsteps; ++st) {
       const int a = prog.a[st];
@@ -564,10 +595,10 @@ __global__ void __launch_bounds__(kThreads)
           TRecord rc;
           *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
           switch (rc.m) {
-            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
-            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
-            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
-            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, g.chunk, KV, kv_eff, acc); break;
+            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
+            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
+            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
+            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
             default: break;
           }
         }
@@ -757,10 +788,10 @@ static GProg<R> make_prog(const RotProgram& rp) {
   return p;
 }
 
-template <typename R, int CS, int NST, bool VJP, int W, typename P>
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P>
 static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
                            int nslabs, size_t smem, cudaStream_t st) {
-  auto kern = k_sweep<R, CS, NST, VJP, W>;
+  auto kern = k_sweep<R, CS, NST, VJP, W, NT, SPLIT>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   static const char* names[2][2][2] = {  // [f64][reverse][beta]
@@ -769,7 +800,7 @@ static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
   ProfScope ps(names[sizeof(R) == 8][VJP][g.dir], st);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nslabs * CS));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -782,14 +813,14 @@ static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
   FS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, prog, X));
 }
 
-template <typename R, int NST, bool VJP, int W, typename P>
+template <typename R, int NST, bool VJP, int W, int NT, typename P>
 static void dispatch_cs(int CS, const SweepGeom& g, const P& prog, const Mat& X,
                         int nslabs, size_t smem, cudaStream_t st) {
   switch (CS) {
-    case 1: launch_sweep_t<R, 1, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
-    case 2: launch_sweep_t<R, 2, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
-    case 4: launch_sweep_t<R, 4, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
-    case 8: launch_sweep_t<R, 8, NST, VJP, W>(g, prog, X, nslabs, smem, st); break;
+    case 1: launch_sweep_t<R, 1, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
+    case 2: launch_sweep_t<R, 2, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
+    case 4: launch_sweep_t<R, 4, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
+    case 8: launch_sweep_t<R, 8, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
     default: FS_REQUIRE(false, FS_ERR_UNSUPPORTED, "cluster size out of range");
   }
 }
@@ -801,24 +832,55 @@ constexpr int window_width() {
   return sizeof(R) == 4 ? (NST == 1 ? 6 : 5) : (NST == 1 ? 5 : 4);
 }
 
+static void set_window_geom(SweepGeom& g, Space* sp, int W) {
+  build_window_tables(sp, W);
+  const Space::Win& wt = sp->win[W];
+  g.orbits = wt.orbits;
+  g.orb_off = wt.off;
+  g.offs = wt.offs;
+  g.offs_stride = (sp->nocc + 1) << W;
+}
+
+// Kernel choice: window sweeps when the orbitals allow a window; forward
+// sweeps on 256 threads when a slab is small enough for two CTAs per SM
+// (their window-step barriers then overlap), else 512; reverse sweeps in
+// split mode (one half-CTA per state) unless the vector spans a cluster.
 template <typename R, int NST, bool VJP>
 static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotProgram& rp,
-                          const Mat& X, int nslabs, size_t smem, cudaStream_t st) {
-  constexpr int W = window_width<R, NST>();
-  if (sthis->norb >= W && sthis->dim > 1) {
-    build_window_tables(sthis, W);
-    SweepGeom g = g0;
-    const Space::Win& wt = sthis->win[W];
-    g.orbits = wt.orbits;
-    g.orb_off = wt.off;
-    g.offs = wt.offs;
-    g.offs_stride = (sthis->nocc + 1) << W;
-    auto prog = make_wprog<R>(rp, sthis->norb, W);
-    dispatch_cs<R, NST, VJP, W>(CS, g, prog, X, nslabs, smem, st);
+                          const Mat& X, int nslabs, size_t smem, bool two_per_sm,
+                          cudaStream_t st) {
+  if constexpr (NST == 1) {
+    constexpr int W = window_width<R, 1>();
+    if (sthis->norb >= W && sthis->dim > 1) {
+      SweepGeom g = g0;
+      set_window_geom(g, sthis, W);
+      auto prog = make_wprog<R>(rp, sthis->norb, W);
+      if (two_per_sm)
+        dispatch_cs<R, NST, VJP, W, 256>(CS, g, prog, X, nslabs, smem, st);
+      else
+        dispatch_cs<R, NST, VJP, W, 512>(CS, g, prog, X, nslabs, smem, st);
+      return;
+    }
   } else {
-    auto prog = make_prog<R>(rp);
-    dispatch_cs<R, NST, VJP, 0>(CS, g0, prog, X, nslabs, smem, st);
+    constexpr int WS = window_width<R, 1>();
+    constexpr int WJ = window_width<R, 2>();
+    if (CS == 1 && sthis->norb >= WS && sthis->dim > 1) {
+      SweepGeom g = g0;
+      set_window_geom(g, sthis, WS);
+      auto prog = make_wprog<R>(rp, sthis->norb, WS);
+      launch_sweep_t<R, 1, NST, VJP, WS, 512, true>(g, prog, X, nslabs, smem, st);
+      return;
+    }
+    if (sthis->norb >= WJ && sthis->dim > 1) {
+      SweepGeom g = g0;
+      set_window_geom(g, sthis, WJ);
+      auto prog = make_wprog<R>(rp, sthis->norb, WJ);
+      dispatch_cs<R, NST, VJP, WJ, 512>(CS, g, prog, X, nslabs, smem, st);
+      return;
+    }
   }
+  auto prog = make_prog<R>(rp);
+  dispatch_cs<R, NST, VJP, 0, 512>(CS, g0, prog, X, nslabs, smem, st);
 }
 
 void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0,
@@ -874,10 +936,14 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   int CS = 1;
   while (CS <= 8 && smem_for(CS, 1) > maxsm) CS *= 2;
   FS_REQUIRE(CS <= 8, FS_ERR_UNSUPPORTED, "state vector too large for a cluster of 8");
-  // vectors per slab: fit shared memory, keep >= 2 slabs per SM when possible
+  // two CTAs per SM for single-state sweeps whose slab fits half the SM
+  const size_t half_sm = (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 - 1024;
+  const bool two_per_sm = nst == 1 && CS == 1 && smem_for(1, 1) <= half_sm;
+  const size_t budget = two_per_sm ? half_sm : maxsm;
+  // vectors per slab: fit the budget, keep >= 2 slabs per SM when possible
   int want = std::max(1, g.nvec / (2 * ctx->prop.multiProcessorCount));
   int lg = 0;
-  while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(CS, 2 << lg) <= maxsm) ++lg;
+  while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(CS, 2 << lg) <= budget) ++lg;
   g.lgKV = lg;
   g.chunk = (g.d + CS - 1) / CS;
   const int KV = 1 << lg;
@@ -885,11 +951,11 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   const size_t smem = std::max<size_t>(smem_for(CS, KV), 16);
   Space* sw = const_cast<Space*>(sthis);
   if (dtype == FS_C64) {
-    if (nst == 1) dispatch_prog<float, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, st);
-    else dispatch_prog<float, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, st);
+    if (nst == 1) dispatch_prog<float, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, two_per_sm, st);
+    else dispatch_prog<float, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, false, st);
   } else {
-    if (nst == 1) dispatch_prog<double, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, st);
-    else dispatch_prog<double, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, st);
+    if (nst == 1) dispatch_prog<double, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, two_per_sm, st);
+    else dispatch_prog<double, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, false, st);
   }
 }
 

@@ -192,3 +192,52 @@ def test_argument_errors(lib):
     with pytest.raises(TypeError):
         lib.apply_orbital_rotation(x.to(torch.complex32) if hasattr(torch, "complex32")
                                    else x.real, np.eye(norb), norb, nelec)
+
+
+# ------------------------------------------------- dense minor-matrix path
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("norb,nelec", [(1, (1, 0)), (4, (2, 2)), (6, (3, 2)), (8, (4, 4)),
+                                        (10, (5, 5)), (12, (6, 6)), (7, (0, 3)), (9, (9, 4)),
+                                        (14, (2, 3))])
+def test_minor_path_parity(lib, dt, norb, nelec):
+    """psi' = M_a psi M_b^T with M[J, I] = det(U[J, I]) (§2.3), forced."""
+    ctx = lib.Context(torch.cuda.current_device())
+    try:
+        ctx.set_rotation_path(lib.FS_ROT_MINORS)
+        g = inputs.rng(13000 + 17 * norb + nelec[0])
+        Ua, Ub = inputs.haar_unitary(norb, g), inputs.haar_unitary(norb, g)
+        v = inputs.random_state(norb, nelec, g)
+        ref = oracle.apply_orbital_rotation(v, Ua, Ub, norb, nelec)
+        got = host(lib.apply_orbital_rotation(dev(v, dt), Ua, norb, nelec, U_b=Ub, ctx=ctx))
+        assert np.max(np.abs(got - ref)) < TOL[dt]
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_autotuned_rotation_path(lib, dt):
+    """FS_ROT_AUTO times both methods once and keeps the faster; either way
+    the result matches the oracle, on the first and on later calls."""
+    ctx = lib.Context(torch.cuda.current_device())
+    try:
+        for norb, nelec in [(8, (4, 4)), (10, (5, 4)), (8, (4, 4))]:
+            g = inputs.rng(13500 + norb)
+            U = inputs.haar_unitary(norb, g)
+            v = inputs.random_state(norb, nelec, g)
+            ref = oracle.apply_orbital_rotation(v, U, None, norb, nelec)
+            got = host(lib.apply_orbital_rotation(dev(v, dt), U, norb, nelec, ctx=ctx))
+            assert np.max(np.abs(got - ref)) < TOL[dt]
+    finally:
+        ctx.close()
+
+
+def test_minor_path_rejects_large_sectors(lib):
+    ctx = lib.Context(torch.cuda.current_device())
+    try:
+        ctx.set_rotation_path(lib.FS_ROT_MINORS)
+        x = dev(inputs.random_state(16, (8, 1), inputs.rng(3)), "c64")
+        with pytest.raises(lib.FsError) as e:
+            lib.apply_orbital_rotation(x, np.eye(16), 16, (8, 1), ctx=ctx)
+        assert e.value.code == -7
+    finally:
+        ctx.close()

@@ -195,3 +195,19 @@ def test_autograd_function_matches_oracle(lib):
     assert np.max(np.abs(At.grad.numpy() - rJa)) < 1e-11
     assert np.max(np.abs(Bt.grad.numpy() - rJb)) < 1e-11
     assert np.max(np.abs(host(vt.grad) - rv)) < 1e-12
+
+
+def test_lucj_vjp_cluster_path_against_oracle(lib):
+    """complex128, N=16 (8,1): an alpha vector of 12870 strings with both
+    states is 412 KB, so the reverse sweeps split it over a 2-CTA cluster
+    (distributed shared memory); gradients against the oracle."""
+    norb, nelec, n_reps = 16, (8, 1), 1
+    K, Jaa, Jab, v, c = _small_case(norb, nelec, n_reps, 14000, False)
+    rK, rJa, rJb, rv = oracle.lucj_vjp(K, Jaa, Jab, c, norb, nelec, vec=v)
+    x = dev(v, "c128")
+    lib.lucj_forward_(x, K, Jaa, Jab, norb, nelec)
+    cg = dev(c, "c128")
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec)
+    assert _rel(dK, rK) < 1e-10 and _rel(dJa, rJa) < 1e-10 and _rel(dJb, rJb) < 1e-10
+    assert np.max(np.abs(host(cg) - rv)) < 1e-12
+    assert np.max(np.abs(host(x) - v)) < 1e-12
