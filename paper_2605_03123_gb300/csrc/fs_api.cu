@@ -154,7 +154,10 @@ static void phase_pass(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
     ph.has_x = 1;
     ph.X = real_mat(J_ab, sa->norb, xscale);
   }
-  launch_phase(sa, sb, vec, dtype, ph, st);
+  if (ph.has_x && phase_tc_supported(dtype, sa))
+    launch_phase_tc(ctx, sa, sb, vec, ph, st);
+  else
+    launch_phase(sa, sb, vec, dtype, ph, st);
 }
 
 static CMat cmat_of(const std::vector<zd>& U, int n) {

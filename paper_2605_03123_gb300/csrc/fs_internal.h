@@ -243,6 +243,11 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
 // Multiply the state by the phase `ph` (one streaming pass).
 void launch_phase(const Space* sa, const Space* sb, void* vec, int dtype,
                   const PhaseDev& ph, cudaStream_t st);
+// The same pass with the cross term contracted on the tensor cores
+// (complex64, norb <= 32; needs scratch for the per-column angle table).
+bool phase_tc_supported(int dtype, const Space* sa);
+void launch_phase_tc(Ctx* ctx, const Space* sa, const Space* sb, void* vec, const PhaseDev& ph,
+                     cudaStream_t st);
 
 // Hartree-Fock closed form (§2.4): psi[i][j] = det(R[I_a(i), 0..n_a-1]) *
 // det(R[I_b(j), 0..n_b-1]) for the N x N matrix R, computed in FP64.

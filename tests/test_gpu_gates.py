@@ -241,3 +241,17 @@ def test_minor_path_rejects_large_sectors(lib):
         assert e.value.code == -7
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("norb,nelec", [(17, (2, 3)), (20, (2, 2)), (16, (8, 1)), (24, (1, 2))])
+def test_diag_coulomb_parity_wide(lib, dt, norb, nelec):
+    """More than 16 orbitals: the complex64 cross term takes two k-steps of
+    the tensor-core contraction."""
+    g = inputs.rng(15000 + norb * 3 + nelec[0])
+    Jaa = inputs.random_symmetric(norb, 1.0, g)
+    Jab = g.normal(0, 1, (norb, norb))
+    v = inputs.random_state(norb, nelec, g)
+    ref = oracle.apply_diag_coulomb_evolution(v, Jaa, Jab, None, 0.45, norb, nelec)
+    got = host(lib.apply_diag_coulomb_evolution(dev(v, dt), Jaa, Jab, 0.45, norb, nelec))
+    assert np.max(np.abs(got - ref)) < TOL[dt]
