@@ -328,12 +328,172 @@ def run_gpu(args):
         "kernels": {k: {"records": v[0], "ms": v[1], "launches": v[2]} for k, v in prof.items()},
         "clocks": clk.summary(),
     }
+    if not args.norb:
+        del vec, cot, vec0, cot0
+        torch.cuda.empty_cache()
+        if args.batch_steps > 0:
+            out["batch"] = run_batch(args, ctx)
+        if args.largest:
+            out["largest"] = run_largest(args, ctx)
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def _timed(fn, reset=None, steps=1):
+    """CUDA-event time of `fn` per call (ms), `reset` run untimed before each."""
+    import torch
+    tot = 0.0
+    for _ in range(steps):
+        if reset:
+            reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def run_batch(args, ctx):
+    """512 LUCJ circuits (norb in {8,10,12,14}, half filling, 2 repetitions,
+    from Hartree-Fock): forward + VJP of all of them as one batched call
+    (complex64, one CUDA graph), against the plain complex128 path run
+    circuit by circuit on a strided sample of the same circuits."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    cir = inputs.batch_circuits(512)
+    amp = [math.comb(c["norb"], c["nelec"][0]) * math.comb(c["norb"], c["nelec"][1]) for c in cir]
+    shape = [(math.comb(c["norb"], c["nelec"][0]), math.comb(c["norb"], c["nelec"][1]))
+             for c in cir]
+    cots0 = [inputs.device_state(c["norb"], c["nelec"], c["cot_seed"], torch.complex64)
+             for c in cir]
+    vecs = [torch.zeros_like(x) for x in cots0]
+    cots = [x.clone() for x in cots0]
+    cfg = [dict(c, from_hf=True) for c in cir]
+
+    def reset():
+        for x, y in zip(cots, cots0):
+            x.copy_(y)
+
+    fsgpu.lucj_batch_(vecs, cots, cfg, ctx=ctx)  # warm-up: plans, tables
+    ctx.profile_start()
+    ms = _timed(lambda: fsgpu.lucj_batch_(vecs, cots, cfg, ctx=ctx), reset, args.batch_steps)
+    prof = ctx.profile_stop()
+    reset()
+    grads64 = fsgpu.lucj_batch_(vecs, cots, cfg, ctx=ctx)
+    del cots
+    fwd64 = vecs
+    fsgpu.lucj_batch_(fwd64, None, cfg, do_vjp=False, ctx=ctx)
+    # plain paths, circuit by circuit, on every k-th circuit
+    sample = list(range(0, len(cir), args.batch_stride))
+    famp = sum(amp[i] for i in sample) / sum(amp)
+
+    def plain(dtype, keep=None):
+        vs = [torch.zeros(shape[i], dtype=dtype, device="cuda") for i in sample]
+        c0 = [cots0[i].to(dtype) for i in sample]
+        cs = [x.clone() for x in c0]
+        res = []
+
+        def run():
+            res.clear()
+            for v, c, x, i in zip(vs, cs, c0, sample):
+                C = cir[i]
+                c.copy_(x)
+                fsgpu.lucj_forward_(v, C["K"], C["J_aa"], C["J_ab"], C["norb"], C["nelec"],
+                                    from_hf=True, ctx=ctx)
+                if keep is not None:
+                    keep.append(v.clone())
+                res.append(fsgpu.lucj_vjp_(v, c, C["K"], C["J_aa"], C["J_ab"], C["norb"],
+                                           C["nelec"], from_hf=True, ctx=ctx))
+        return run, res
+
+    run128, _ = plain(torch.complex128)
+    run128()  # warm-up
+    ms128 = _timed(run128)
+    del run128
+    out128 = []
+    run128k, g128 = plain(torch.complex128, out128)
+    run128k()
+    run64, _ = plain(torch.complex64)
+    run64()
+    ms64p = _timed(run64)
+    fwd_err = max(float((fwd64[i].to(torch.complex128) - o).abs().max().item())
+                  for i, o in zip(sample, out128))
+    grad_rel = max(float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                   for i, g in zip(sample, g128) for a, b in zip(grads64[i], g))
+    n = len(cir)
+    rate = n / (ms / 1e3)
+    # plain-path rates scaled to the whole batch by the sample's share of
+    # the amplitudes
+    rate128 = n * famp / (ms128 / 1e3)
+    return {"workload": "lucj_batch_512_circuits_norb8-14_half_filling_2reps",
+            "circuits": n, "amplitudes_total": sum(amp), "state": "complex64",
+            "circuits_per_s": rate, "ms_per_step": ms, "steps": args.batch_steps,
+            "graph_launches_per_step": 1,
+            "kernels": {k: {"records": v[0], "ms": v[1], "launches": v[2]}
+                        for k, v in prof.items()},
+            "plain_sample": "every %d-th circuit (%d circuits, %.3f of the amplitudes)"
+                            % (args.batch_stride, len(sample), famp),
+            "plain_c128_circuits_per_s_equiv": rate128,
+            "plain_c64_circuits_per_s_equiv": n * famp / (ms64p / 1e3),
+            "c64_batched_speedup_vs_plain_c128": rate / rate128,
+            "c64_vs_c128_fwd_max_abs": fwd_err, "c64_vs_c128_grad_rel": grad_rel}
+
+
+def run_largest(args, ctx):
+    """N=18 (9,9), one LUCJ repetition from Hartree-Fock: complex64 forward +
+    VJP (2.36e9 amplitudes, 18.9 GB per state), complex128 forward beside."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    w = inputs.largest_state()
+    N, ne = w["norb"], w["nelec"]
+    K, Ja, Jb = w["K"], w["J_aa"], w["J_ab"]
+    v = inputs.device_state(N, ne, 1, torch.complex64)
+    v.zero_()
+    cot = inputs.device_state(N, ne, w["cot_seed"], torch.complex64)
+    cot0 = cot.clone()
+    fsgpu.lucj_forward_(v, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)  # warm-up
+    norm_err = abs(float(torch.linalg.vector_norm(v).item()) - 1.0)
+    fsgpu.lucj_vjp_(v, cot, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+
+    def step():
+        fsgpu.lucj_forward_(v, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+        fsgpu.lucj_vjp_(v, cot, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+
+    ms = _timed(step, lambda: cot.copy_(cot0), args.largest)
+    rec = float(v[0, 0].real.item()) - 1.0
+    rec_err = max(abs(rec), float(v.abs().flatten()[1:].max().item()))
+    # <A^dag g, psi_in> = <g, A psi_in>: the VJP of a linear map at HF is
+    # the HF amplitude of A^dag g
+    fsgpu.lucj_forward_(v, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+    lhs = sum(complex(torch.vdot(cot0[i:i + 4096].flatten(), v[i:i + 4096].flatten()).item())
+              for i in range(0, v.shape[0], 4096))
+    c2 = cot0.clone()
+    fsgpu.lucj_vjp_(v, c2, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+    rhs = complex(c2[0, 0].item()).conjugate()
+    out64 = v
+    fsgpu.lucj_forward_(out64, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+    del cot, cot0, c2
+    torch.cuda.empty_cache()
+    v2 = torch.zeros(out64.shape, dtype=torch.complex128, device="cuda")
+    fsgpu.lucj_forward_(v2, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx)
+    ms128 = _timed(lambda: fsgpu.lucj_forward_(v2, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx))
+    ms64f = _timed(lambda: fsgpu.lucj_forward_(out64, K, Ja, Jb, N, ne, from_hf=True, ctx=ctx))
+    err = float((out64.to(torch.complex128) - v2).abs().max().item())
+    del v2, out64, v
+    torch.cuda.empty_cache()
+    return {"workload": "lucj_norb18_nelec9_9_1rep_from_hf", "amplitudes": math.comb(18, 9) ** 2,
+            "state": "complex64", "fwd_vjp_ms": ms, "layers_per_s": 1e3 / ms,
+            "fwd_ms_c64": ms64f, "fwd_ms_c128": ms128, "c64_fwd_speedup": ms128 / ms64f,
+            "forward_norm_err": norm_err, "recovered_input_max_abs_err": rec_err,
+            "vjp_inner_product_identity_abs_err": abs(lhs - rhs),
+            "c64_vs_c128_fwd_max_abs": err}
 
 
 # ------------------------------------------------------------------ oracle
@@ -419,6 +579,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--c128-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=2,
+                    help="timed calls of the 512-circuit batch (0 skips it)")
+    ap.add_argument("--batch-stride", type=int, default=4,
+                    help="plain-path sample of the batch: every k-th circuit")
+    ap.add_argument("--largest", type=int, default=1,
+                    help="timed steps of the N=18 (9,9) state (0 skips it)")
     ap.add_argument("--norb", type=int, default=0,
                     help="profiling only: another sector size instead of the N=16 workload")
     ap.add_argument("--nalpha", type=int, default=0)

@@ -200,6 +200,24 @@ int fs_lucj_vjp(fs_ctx *ctx, const fs_lucj *op, void *vec, void *cot,
                 int dtype, double *dK, double *dJ_aa, double *dJ_ab,
                 void *stream);
 
+/* Batched LUCJ (the ansatz of fs_lucj_forward, many independent circuits,
+ * uneven sectors): ops[c], vecs[c], cots[c] describe circuit c exactly as
+ * for fs_lucj_forward (and, when do_vjp, fs_lucj_vjp, which then follows
+ * the forward pass: vec ends as the recomputed input, cot as dL/dpsi_in,
+ * and dK[c], dJ_aa[c], dJ_ab[c] receive the gradients; any of these arrays
+ * or entries may be NULL to skip).  Every stage of the circuits runs once
+ * for all of them: each sweep is one persistent kernel launch over a work
+ * queue of (circuit, slab) items, largest circuits first, and the whole
+ * stage sequence is one captured CUDA graph.  Requirements: one dtype, the
+ * same n_reps for all circuits, 6 <= norb <= 32, 2 <= C(norb, n_s) <= 65535.
+ * Host outputs; synchronizes the stream when do_vjp.  The paper applies
+ * its gates to one state at a time; batching is a deployment form of the
+ * same operations. */
+int fs_lucj_batch(fs_ctx *ctx, int n_circuits, const fs_lucj *ops,
+                  void *const *vecs, void *const *cots, int dtype, int do_vjp,
+                  double *const *dK, double *const *dJ_aa,
+                  double *const *dJ_ab, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

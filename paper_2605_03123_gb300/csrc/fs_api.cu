@@ -296,6 +296,7 @@ int fs_destroy(fs_ctx* ctx) {
     for (auto& kv : ctx->spaces) free_space(kv.second);
     for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
     cudaFree(ctx->d_status);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
   });
 }
@@ -628,5 +629,28 @@ extern "C" int fs_lucj_vjp(fs_ctx* ctx, const fs_lucj* op, void* vec, void* cot,
     current_ctx() = ctx;
     FS_CUDA(cudaSetDevice(ctx->device));
     lucj_vjp_impl(ctx, op, vec, cot, dtype, dK, dJ_aa, dJ_ab, (cudaStream_t)stream);
+  });
+}
+
+extern "C" int fs_lucj_batch(fs_ctx* ctx, int n_circuits, const fs_lucj* ops, void* const* vecs,
+                             void* const* cots, int dtype, int do_vjp, double* const* dK,
+                             double* const* dJ_aa, double* const* dJ_ab, void* stream) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr && ops != nullptr && vecs != nullptr, FS_ERR_ARG, "null argument");
+    FS_REQUIRE(n_circuits >= 1, FS_ERR_ARG, "n_circuits must be >= 1");
+    FS_REQUIRE(dtype == FS_C64 || dtype == FS_C128, FS_ERR_ARG, "dtype must be FS_C64 or FS_C128");
+    FS_REQUIRE(!do_vjp || cots != nullptr, FS_ERR_ARG, "null cotangent array");
+    for (int c = 0; c < n_circuits; ++c) {
+      const fs_lucj* op = &ops[c];
+      FS_REQUIRE(op->norb >= 1 && op->norb <= kMaxNorb && op->n_alpha >= 0 &&
+                     op->n_alpha <= op->norb && op->n_beta >= 0 && op->n_beta <= op->norb &&
+                     op->n_reps >= 0 && (op->n_reps == 0 || (op->K && op->J_aa && op->J_ab)),
+                 FS_ERR_ARG, "bad circuit description");
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    lucj_batch(ctx, n_circuits, ops, vecs, cots, dtype, do_vjp, dK, dJ_aa, dJ_ab,
+               (cudaStream_t)stream);
   });
 }

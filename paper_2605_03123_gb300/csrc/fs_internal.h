@@ -138,6 +138,10 @@ struct Ctx {
   std::map<std::pair<int, int>, Space*> spaces;
   std::map<std::string, Scratch> scratch;
   int* d_status = nullptr;  // device status word
+  // private non-blocking stream on which batched launches are captured into
+  // a graph (a capture cannot run on the legacy default stream); the graph
+  // itself is launched on the caller's stream
+  cudaStream_t capture_stream = nullptr;
   std::mutex mu;
 };
 
@@ -213,6 +217,82 @@ struct PhaseDev {
 //                                                    - t sum_{p in I} lam[p])).
 void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& f,
                          cudaStream_t st);
+
+// Window program: step s applies Givens g0[s] .. g0[s+1]-1, all acting on
+// orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
+// index of the rotated pair (p, p+1).
+template <typename R>
+struct WProg {
+  int nsteps;
+  int8_t a[kMaxGivens];
+  int16_t g0[kMaxGivens + 1];
+  int8_t u[kMaxGivens];
+  R c[kMaxGivens];
+  R sr[kMaxGivens];
+  R si[kMaxGivens];
+};
+
+// Geometry and phase/reduction pointers of one sweep launch (one job of a
+// batched launch).
+struct SweepGeom {
+  void* st[2];
+  int64_t d_b;  // row stride of the state
+  int dir;      // 0: alpha, vectors are columns; 1: beta, vectors are rows
+  int d;        // vector length (strings of the rotated spin)
+  int nvec;     // number of vectors (strings of the other spin)
+  int lgKV;     // log2 of vectors per slab
+  int chunk;    // vector elements held by one CTA of the cluster
+  const uint32_t* pairs;
+  int npp;
+  const uint32_t* masks_this;
+  const uint32_t* masks_other;
+  int norb;
+  int nchunk;  // 8-bit chunks of a string mask
+  const void* ea_this;
+  const void* ea_other;
+  int has_x;  // cross angles X[p_alpha][q_beta] are passed separately
+  // reverse mode (dual state: st[0] = psi, st[1] = cotangent g)
+  const void* ea2_this;   // second phase (applied after the reductions)
+  const void* ea2_other;
+  const uint32_t* xpairs;  // E_pq pair lists of the rotated spin
+  const uint32_t* xsign;
+  const int* xcount;
+  int nx;
+  double* T;  // [norb][norb] complex accumulator: += <g| E_pq |psi>
+  void* W;    // [d_a][d_b] real: Im(conj(g) psi), or null
+  // transition-reduction passes of the rotated spin (reverse mode, N >= 4)
+  const TPassDev* tpass;
+  const TRecord* trec;
+  int npass;
+  // window tables of the rotated spin (window kernels only)
+  const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
+  const int* orb_off;      // [npos + 1] start of each position's list
+  const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
+  int offs_stride;         // (nocc + 1) << W
+};
+
+struct SweepJob {
+  SweepGeom g;
+  const void* prog;  // WProg<R> in device memory
+  const Mat* X;      // device memory
+  int item0;         // first work item of this job in the batched launch
+};
+struct BatchSweepPlan {
+  SweepGeom g;
+  int nslabs = 0;
+  size_t smem = 0;
+  std::vector<unsigned char> prog;  // WProg<R> bytes
+};
+size_t wprog_bytes(int dtype);
+void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* st1, int nst,
+                      int dtype, const RotProgram& rp, const PhaseDev& ph, const struct RevArgs* rev,
+                      size_t budget, BatchSweepPlan& out);
+// jobs == nullptr: only set the kernel's shared-memory attribute.
+void launch_sweep_batch(Ctx* ctx, int dtype, int nst, const SweepJob* jobs, int njobs, int total,
+                        int* counter, size_t smem, cudaStream_t st);
+void lucj_batch(Ctx* ctx, int n, const fs_lucj* ops, void* const* vecs, void* const* cots,
+                int dtype, int do_vjp, double* const* dK, double* const* dJaa,
+                double* const* dJab, cudaStream_t st);
 
 // Reverse-mode extras of a dual-state sweep (st0 = psi, st1 = cotangent).
 struct RevArgs {

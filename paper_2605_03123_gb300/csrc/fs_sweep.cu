@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -31,57 +32,6 @@ struct GProg {
   R c[kMaxGivens];
   R sr[kMaxGivens];
   R si[kMaxGivens];
-};
-
-// Window program: step s applies Givens g0[s] .. g0[s+1]-1, all acting on
-// orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
-// index of the rotated pair (p, p+1).
-template <typename R>
-struct WProg {
-  int nsteps;
-  int8_t a[kMaxGivens];
-  int16_t g0[kMaxGivens + 1];
-  int8_t u[kMaxGivens];
-  R c[kMaxGivens];
-  R sr[kMaxGivens];
-  R si[kMaxGivens];
-};
-
-struct SweepGeom {
-  void* st[2];
-  int64_t d_b;  // row stride of the state
-  int dir;      // 0: alpha, vectors are columns; 1: beta, vectors are rows
-  int d;        // vector length (strings of the rotated spin)
-  int nvec;     // number of vectors (strings of the other spin)
-  int lgKV;     // log2 of vectors per slab
-  int chunk;    // vector elements held by one CTA of the cluster
-  const uint32_t* pairs;
-  int npp;
-  const uint32_t* masks_this;
-  const uint32_t* masks_other;
-  int norb;
-  int nchunk;  // 8-bit chunks of a string mask
-  const void* ea_this;
-  const void* ea_other;
-  int has_x;  // cross angles X[p_alpha][q_beta] are passed separately
-  // reverse mode (dual state: st[0] = psi, st[1] = cotangent g)
-  const void* ea2_this;   // second phase (applied after the reductions)
-  const void* ea2_other;
-  const uint32_t* xpairs;  // E_pq pair lists of the rotated spin
-  const uint32_t* xsign;
-  const int* xcount;
-  int nx;
-  double* T;  // [norb][norb] complex accumulator: += <g| E_pq |psi>
-  void* W;    // [d_a][d_b] real: Im(conj(g) psi), or null
-  // transition-reduction passes of the rotated spin (reverse mode, N >= 4)
-  const TPassDev* tpass;
-  const TRecord* trec;
-  int npass;
-  // window tables of the rotated spin (window kernels only)
-  const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
-  const int* orb_off;      // [npos + 1] start of each position's list
-  const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
-  int offs_stride;         // (nocc + 1) << W
 };
 
 // Subsets of a W-orbital window holding M electrons, in ascending-mask
@@ -396,22 +346,20 @@ __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
 
 // W == 0: one shared-memory pass per Givens rotation (pair lists);
 // W > 0: one pass per window step, orbits rotated in registers.
+// One slab of a sweep (see launch_sweep): load, Givens rotations, epilogue.
 // NT threads per CTA.  SPLIT (two states, no cluster): during the Givens
 // phase the first half of the CTA rotates state 0 and the second half state
 // 1, each half synchronising on its own named barrier.
-template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
-    k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
-            const __grid_constant__ Mat X) {
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P>
+__device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, const Mat& X,
+                                           const int slab, const int rank,
+                                           unsigned char* smraw) {
   static_assert(!VJP || NST == 2, "reverse mode carries two states");
   static_assert(!SPLIT || (NST == 2 && CS == 1 && W > 0), "split mode: two states, one CTA");
   constexpr int kThreads = NT;
   using C = cx_t<R>;
-  extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int KV = 1 << g.lgKV;
-  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int slab = blockIdx.x / CS;
   const int v0 = slab * KV;
   const int kv_eff = min(KV, g.nvec - v0);
   const int e0 = rank * g.chunk;
@@ -708,6 +656,43 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
   }
 }
 
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
+    k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
+            const __grid_constant__ Mat X) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  sweep_body<R, CS, NST, VJP, W, NT, SPLIT>(g, prog, X, blockIdx.x / CS, rank, smraw);
+}
+
+// Batched sweep: one persistent launch over the slabs of many jobs (one job
+// per circuit), taken from an atomic work counter in job order.
+template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
+    k_sweep_batch(const SweepJob* jobs, int njobs, int total, int* counter) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_item, s_job;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(counter, 1);
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {  // last job with item0 <= it
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item0 <= it) lo = mid; else hi = mid - 1;
+      }
+      s_item = it;
+      s_job = lo;
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= total) break;
+    const SweepJob& J = jobs[s_job];
+    sweep_body<R, 1, NST, VJP, W, NT, SPLIT>(J.g, *reinterpret_cast<const WProg<R>*>(J.prog),
+                                             *J.X, it - J.item0, 0, smraw);
+    __syncthreads();
+  }
+}
+
 // Transition-reduction passes of a space (built once, on the host; see
 // tpass_tables_host).
 static void build_tpass_tables(Space* sp) {
@@ -956,6 +941,123 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   } else {
     if (nst == 1) dispatch_prog<double, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, two_per_sm, st);
     else dispatch_prog<double, 2, true>(sw, CS, g, rp, ph.X, nslabs, smem, false, st);
+  }
+}
+
+// ------------------------------------------------------- batched sweeps
+size_t wprog_bytes(int dtype) {
+  return dtype == FS_C64 ? sizeof(WProg<float>) : sizeof(WProg<double>);
+}
+
+int batch_window(int dtype, int nst) {
+  return dtype == FS_C64 ? (nst == 1 ? window_width<float, 1>() : window_width<float, 1>())
+                         : (nst == 1 ? window_width<double, 1>() : window_width<double, 1>());
+}
+
+// One circuit's sweep as a job of a batched launch: one CTA per slab (no
+// cluster), window program for the batch window width, slab sized to
+// `budget` bytes of shared memory.
+void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* st1, int nst,
+                      int dtype, const RotProgram& rp, const PhaseDev& ph, const RevArgs* rev,
+                      size_t budget, BatchSweepPlan& out) {
+  Space* sthis = dir == 0 ? sa : sb;
+  Space* sother = dir == 0 ? sb : sa;
+  const int W = batch_window(dtype, nst);
+  FS_REQUIRE(sthis->norb >= W && sthis->dim > 1 && sthis->dim <= kMaxSweepDim,
+             FS_ERR_UNSUPPORTED, "batched sweeps need norb >= 6 and 2 <= dim <= 65535");
+  SweepGeom& g = out.g;
+  g = SweepGeom{};
+  g.st[0] = st0;
+  g.st[1] = st1;
+  g.d_b = sb->dim;
+  g.dir = dir;
+  g.d = (int)sthis->dim;
+  g.nvec = (int)sother->dim;
+  g.pairs = sthis->pairs;
+  g.npp = sthis->npp;
+  g.masks_this = sthis->masks;
+  g.masks_other = sother->masks;
+  g.norb = sthis->norb;
+  g.nchunk = (sthis->norb + 7) / 8;
+  g.ea_this = dir == 0 ? ph.ea_a : ph.ea_b;
+  g.ea_other = dir == 0 ? ph.ea_b : ph.ea_a;
+  g.has_x = ph.has_x;
+  if (rev) {
+    g.ea2_this = dir == 0 ? rev->ea2_a : rev->ea2_b;
+    g.ea2_other = dir == 0 ? rev->ea2_b : rev->ea2_a;
+    g.T = rev->T;
+    g.W = rev->W;
+    build_tpass_tables(sthis);
+    g.tpass = sthis->tpass;
+    g.trec = sthis->trec;
+    g.npass = sthis->npass;
+  }
+  set_window_geom(g, sthis, W);
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  const size_t tab_per_kv = ph.has_x ? g.nchunk * 256 * csz : 0;
+  const size_t fixed = ph.has_x ? kMaxOrb * sizeof(double) : 0;
+  const size_t tsum = (size_t)g.npass * 32 * (csz / 2);
+  auto smem_for = [&](int KV) {
+    return (size_t)KV * ((size_t)g.d * csz * nst + tab_per_kv + fixed) + tsum;
+  };
+  FS_REQUIRE(smem_for(1) <= budget, FS_ERR_UNSUPPORTED, "batched sweep slab does not fit");
+  int want = std::max(1, g.nvec / 8);
+  int lg = 0;
+  while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(2 << lg) <= budget) ++lg;
+  g.lgKV = lg;
+  g.chunk = g.d;
+  out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
+  out.smem = smem_for(1 << lg);
+  out.prog.resize(wprog_bytes(dtype));
+  if (dtype == FS_C64) {
+    auto w = make_wprog<float>(rp, sthis->norb, W);
+    memcpy(out.prog.data(), &w, sizeof(w));
+  } else {
+    auto w = make_wprog<double>(rp, sthis->norb, W);
+    memcpy(out.prog.data(), &w, sizeof(w));
+  }
+}
+
+template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT>
+static void launch_batch_t(const SweepJob* jobs, int njobs, int total, int* counter, size_t smem,
+                           int grid, cudaStream_t st) {
+  auto kern = k_sweep_batch<R, NST, VJP, W, NT, SPLIT>;
+  if (!jobs) {  // attribute only (called before a stream capture); only ever
+                // raised, since several stages share one kernel
+    cudaFuncAttributes fa;
+    FS_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return;
+  }
+  kern<<<grid, NT, smem, st>>>(jobs, njobs, total, counter);
+  FS_CUDA(cudaGetLastError());
+}
+
+void launch_sweep_batch(Ctx* ctx, int dtype, int nst, const SweepJob* jobs, int njobs, int total,
+                        int* counter, size_t smem, cudaStream_t st) {
+  const int sms = ctx->prop.multiProcessorCount;
+  const size_t half_sm = (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 - 1024;
+  if (dtype == FS_C64) {
+    constexpr int W = window_width<float, 1>();
+    if (nst == 1) {
+      if (smem <= half_sm)
+        launch_batch_t<float, 1, false, W, 256, false>(jobs, njobs, total, counter, smem, 2 * sms, st);
+      else
+        launch_batch_t<float, 1, false, W, 512, false>(jobs, njobs, total, counter, smem, sms, st);
+    } else {
+      launch_batch_t<float, 2, true, W, 512, true>(jobs, njobs, total, counter, smem, sms, st);
+    }
+  } else {
+    constexpr int W = window_width<double, 1>();
+    if (nst == 1) {
+      if (smem <= half_sm)
+        launch_batch_t<double, 1, false, W, 256, false>(jobs, njobs, total, counter, smem, 2 * sms, st);
+      else
+        launch_batch_t<double, 1, false, W, 512, false>(jobs, njobs, total, counter, smem, sms, st);
+    } else {
+      launch_batch_t<double, 2, true, W, 512, true>(jobs, njobs, total, counter, smem, sms, st);
+    }
   }
 }
 

@@ -58,6 +58,8 @@ SIGNATURES = {
     "fs_apply_diag_coulomb_evolution_noalloc": [_P, _I, _P, _P, _P, _D, _I, _I, _I, _P],
     "fs_lucj_forward": [_P, ctypes.POINTER(LUCJ), _P, _I, _P],
     "fs_lucj_vjp": [_P, ctypes.POINTER(LUCJ), _P, _P, _I, _P, _P, _P, _P],
+    "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
+                      _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
 }
 
 _lib = None
@@ -290,3 +292,41 @@ def lucj_vjp_(vec, cot, K, J_aa, J_ab, norb, nelec, from_hf=False, ctx=None):
         ctx.handle, ctypes.byref(op), _P(vec.data_ptr()), _P(cot.data_ptr()),
         _dtype_code(vec), _ptr(dK), _ptr(dJa), _ptr(dJb), _stream_ptr()))
     return dK, dJa, dJb
+
+
+def lucj_batch_(vecs, cots, circuits, do_vjp=True, ctx=None):
+    """Forward pass (and, with do_vjp, the VJP) of many independent LUCJ
+    circuits in one CUDA graph.  circuits[c] = dict(K, J_aa, J_ab, norb,
+    nelec, from_hf); vecs[c] / cots[c] are that circuit's state and
+    cotangent tensors (one dtype for all), updated in place exactly as by
+    lucj_forward_ followed by lucj_vjp_.  All circuits share n_reps.
+    Returns [(dK, dJ_aa, dJ_ab)] (None without do_vjp)."""
+    n = len(circuits)
+    if len(vecs) != n or (do_vjp and len(cots) != n):
+        raise ValueError("one state (and cotangent) per circuit")
+    dt = _dtype_code(vecs[0])
+    ctx = ctx or context(vecs[0].device.index)
+    ops = (LUCJ * n)()
+    keep, grads = [], []
+    pK, pA, pB = (_P * n)(), (_P * n)(), (_P * n)()
+    for c, cir in enumerate(circuits):
+        norb, nelec = cir["norb"], tuple(cir["nelec"])
+        _check_state(vecs[c], norb, nelec)
+        if _dtype_code(vecs[c]) != dt:
+            raise TypeError("all states of a batch need one dtype")
+        if do_vjp:
+            _check_state(cots[c], norb, nelec)
+        op, k = _lucj_struct(cir["K"], cir["J_aa"], cir["J_ab"], norb, nelec,
+                             cir.get("from_hf", False))
+        ops[c] = op
+        keep.append(k)
+        r = op.n_reps
+        g = (np.zeros((r, norb, norb), np.complex128), np.zeros((r, norb, norb)),
+             np.zeros((r, norb, norb)))
+        grads.append(g)
+        pK[c], pA[c], pB[c] = g[0].ctypes.data, g[1].ctypes.data, g[2].ctypes.data
+    pv = (_P * n)(*[v.data_ptr() for v in vecs])
+    pc = (_P * n)(*[x.data_ptr() for x in cots]) if do_vjp else (_P * n)()
+    _check("fs_lucj_batch", load_library().fs_lucj_batch(
+        ctx.handle, n, ops, pv, pc, dt, int(bool(do_vjp)), pK, pA, pB, _stream_ptr()))
+    return grads if do_vjp else [None] * n

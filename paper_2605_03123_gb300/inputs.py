@@ -91,7 +91,7 @@ def plain_small(index=0):
                 J_ab=random_symmetric(norb, 1.0, g), t=0.7)
 
 
-def lucj_layers(norb, nelec, n_layers, sigma_j, t, seed, from_hf=False):
+def lucj_layers(norb, nelec, n_layers, sigma_j, t, seed, from_hf=False, with_cot=True):
     """LUCJ parameters with Haar-random rotations: K_k = log(U_k) for Haar U_k,
     J_k = t * N(0, sigma_j) symmetric (the evolution time folded into J)."""
     g = rng(seed)
@@ -101,9 +101,9 @@ def lucj_layers(norb, nelec, n_layers, sigma_j, t, seed, from_hf=False):
         Jaa.append(t * random_symmetric(norb, sigma_j, g))
         Jab.append(t * random_symmetric(norb, sigma_j, g))
     vec = None if from_hf else random_state(norb, nelec, g)
-    cot = random_cotangent(norb, nelec, g)
+    cot = random_cotangent(norb, nelec, g) if with_cot else None
     return dict(norb=norb, nelec=nelec, K=np.array(Ks), J_aa=np.array(Jaa),
-                J_ab=np.array(Jab), vec=vec, cot=cot)
+                J_ab=np.array(Jab), vec=vec, cot=cot, cot_seed=seed + 500000)
 
 
 def plain_at_scale(index=0):
@@ -127,19 +127,42 @@ def lucj_small(index=0):
                 J_ab=np.array(Jab), vec=None, cot=random_cotangent(norb, nelec, g))
 
 
-def batch_circuits(n_circuits=512, index=0):
+def batch_circuits(n_circuits=512, index=0, with_cot=False):
     """Circuits with norb uniform in {8, 10, 12, 14} at half filling, 2
-    repetitions each from Hartree-Fock, parameters as in `plain_at_scale`."""
+    repetitions each from Hartree-Fock, parameters as in `plain_at_scale`.
+    Cotangents (1.6e9 amplitudes over 512 circuits) are drawn on the device
+    from each circuit's `cot_seed` unless `with_cot`."""
     g = rng(1000 * 4 + index)
     norbs = g.choice([8, 10, 12, 14], size=n_circuits)
     out = []
     for c, n in enumerate(norbs):
         n = int(n)
         out.append(lucj_layers(n, (n // 2, n // 2), 2, 0.5, 0.3,
-                               1000 * 4 + 100000 + 1000 * index + c, from_hf=True))
+                               1000 * 4 + 100000 + 1000 * index + c, from_hf=True,
+                               with_cot=with_cot))
     return out
 
 
 def largest_state(index=0):
-    """N=18 (9,9), one repetition from Hartree-Fock, J ~ N(0, 0.2)."""
-    return lucj_layers(18, (9, 9), 1, 0.2, 1.0, 1000 * 5 + index, from_hf=True)
+    """N=18 (9,9), one repetition from Hartree-Fock, J ~ N(0, 0.2).  The
+    2.36e9-amplitude cotangent is not drawn here: `device_state` draws it on
+    the GPU from its own seed."""
+    g = rng(1000 * 5 + index)
+    K = antihermitian_log(haar_unitary(18, g))[None]
+    return dict(norb=18, nelec=(9, 9), K=K, J_aa=random_symmetric(18, 0.2, g)[None],
+                J_ab=random_symmetric(18, 0.2, g)[None], vec=None, cot=None,
+                cot_seed=1000 * 5 + 500 + index)
+
+
+def device_state(norb, nelec, seed, dtype, device="cuda"):
+    """A normalised random state drawn on the device (torch Philox generator
+    seeded with `seed`), for states too large to draw on the host."""
+    import torch
+    da, db = dims(norb, nelec)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    real = torch.float32 if dtype == torch.complex64 else torch.float64
+    v = torch.randn((da, db, 2), generator=gen, device=device, dtype=real)
+    v = torch.view_as_complex(v)
+    v /= torch.linalg.vector_norm(v)
+    return v

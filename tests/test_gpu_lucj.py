@@ -211,3 +211,45 @@ def test_lucj_vjp_cluster_path_against_oracle(lib):
     assert _rel(dK, rK) < 1e-10 and _rel(dJa, rJa) < 1e-10 and _rel(dJb, rJb) < 1e-10
     assert np.max(np.abs(host(cg) - rv)) < 1e-12
     assert np.max(np.abs(host(x) - v)) < 1e-12
+
+
+def _vdot_rows(a, b, rows=4096):
+    """<a, b> over row blocks (one cuBLAS dot is limited to 2^31 elements)."""
+    return sum(complex(torch.vdot(a[i:i + rows].flatten(), b[i:i + rows].flatten()).item())
+               for i in range(0, a.shape[0], rows))
+
+
+def test_lucj_norb18_properties(lib):
+    """N=18 (9,9), one repetition from Hartree-Fock (2.36e9 amplitudes; the
+    sweeps run on 4- and 8-CTA clusters): unit norm, the recovered input is
+    Hartree-Fock, <g, psi_out> equals the conjugate HF amplitude of
+    dL/dpsi_in, and complex64 agrees with complex128 (forward state and
+    gradients)."""
+    w = inputs.largest_state()
+    N, ne = w["norb"], w["nelec"]
+    K, Ja, Jb = w["K"], w["J_aa"], w["J_ab"]
+    res = {}
+    for dt in (torch.complex64, torch.complex128):
+        cot0 = inputs.device_state(N, ne, w["cot_seed"], torch.complex64).to(dt)
+        x = torch.zeros_like(cot0)
+        lib.lucj_forward_(x, K, Ja, Jb, N, ne, from_hf=True)
+        assert abs(float(torch.linalg.vector_norm(x).item()) - 1) < 1e-4
+        lhs = _vdot_rows(cot0, x)
+        fwd = x[:64, :].clone(), x[-64:, :].clone()
+        cg = cot0.clone()
+        del cot0
+        g = lib.lucj_vjp_(x, cg, K, Ja, Jb, N, ne, from_hf=True)
+        assert abs(float(x[0, 0].real.item()) - 1) < 1e-5
+        x[0, 0] = 0
+        assert float(x.abs().max().item()) < 1e-5
+        rhs = complex(cg[0, 0].item()).conjugate()
+        assert abs(lhs - rhs) < 1e-4
+        res[dt] = fwd, g
+        del x, cg
+        torch.cuda.empty_cache()
+    (f64a, f64b), g64 = res[torch.complex64]
+    (f128a, f128b), g128 = res[torch.complex128]
+    assert float((f64a.to(torch.complex128) - f128a).abs().max().item()) < 2e-5
+    assert float((f64b.to(torch.complex128) - f128b).abs().max().item()) < 2e-5
+    for a, b in zip(g64, g128):
+        assert _rel(a, b) < 1e-3
