@@ -178,11 +178,20 @@ std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W) {
 // of O u S (S inside the window) is R_O + F[a][c_lo][S], where R_O sums
 // C(o_k, k+1) over O's orbitals with their index k in the full string and F
 // sums the same terms over S's orbitals (combinatorial-number-system rank).
+// Top-3 group of a configuration: the occupation of orbitals N-1, N-2, N-3
+// read as a 3-bit number (the strings of one group form a contiguous range
+// of addresses, since addresses follow the integer order of the masks).
+static inline int top3_group(uint32_t mask, int N) {
+  return N >= 3 ? (int)((mask >> (N - 3)) & 7u) : 0;
+}
+
 void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
-                        std::vector<int>& off, std::vector<uint16_t>& offs) {
+                        std::vector<int>& off, std::vector<uint16_t>& offs,
+                        std::vector<int>& goff) {
   const int npos = N - W + 1;
   orbits.clear();
   off.assign(npos + 1, 0);
+  goff.assign((size_t)npos * 9, 0);
   offs.assign((size_t)npos * (n + 1) << W, 0);
   auto C = [](int a, int b) -> uint64_t {
     if (b < 0 || b > a) return 0;
@@ -192,6 +201,7 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
   };
   for (int a = 0; a < npos; ++a) {
     off[a] = (int)orbits.size();
+    std::vector<std::pair<int, uint32_t>> keyed;  // (top-3 group, descriptor)
     std::vector<int> out;
     for (int p = 0; p < N; ++p)
       if (p < a || p >= a + W) out.push_back(p);
@@ -204,9 +214,11 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
       while (true) {
         int clo = 0, k = 0;
         uint64_t ro = 0;
+        uint32_t omask = 0;
         for (int i = 0; i < no; ++i)
           if ((x >> i) & 1) {
             int o = out[i];
+            omask |= 1u << o;
             if (o < a) {
               ro += C(o, k + 1);
               ++clo;
@@ -215,12 +227,24 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
             }
             ++k;
           }
-        orbits.push_back((uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
+        keyed.emplace_back(top3_group(omask, N),
+                           (uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), r = x + c;
         x = (((r ^ x) >> 2) / c) | r;
         if (x >> no) break;
       }
+    }
+    // grouped by the occupation of the top three orbitals (for windows
+    // clear of them, every string of an orbit lies in that group's address
+    // range), sorted by m inside a group
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const auto& u, const auto& v) { return u.first < v.first; });
+    int* go = &goff[(size_t)a * 9];
+    for (int k = 0; k <= 8; ++k) go[k] = off[a];
+    for (const auto& kd : keyed) {
+      orbits.push_back(kd.second);
+      for (int k = kd.first + 1; k <= 8; ++k) ++go[k];
     }
     for (int clo = 0; clo <= n; ++clo)
       for (int S = 0; S < (1 << W); ++S) {
@@ -355,6 +379,7 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
   };
   for (auto& ps : passes) {
     ps.rec0 = (int)recs.size();
+    std::vector<std::pair<int, TRecord>> keyed;  // (top-3 group of O, record)
     uint32_t qmask = 0;
     for (int i = 0; i < 4; ++i) qmask |= 1u << ps.q[i];
     std::vector<int> out;
@@ -386,12 +411,20 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
           g |= (uint8_t)(acc << (j + 1));  // bit j+1: parity of O before q_{j+1}
         }
         r.gbits = g;
-        recs.push_back(r);
+        keyed.emplace_back(top3_group(omask, N), r);
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), rr = x + c;
         x = (((rr ^ x) >> 2) / c) | rr;
         if (x >> no) break;
       }
+    }
+    // grouped by the top-3 occupation of O, sorted by m inside a group
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const auto& u, const auto& v) { return u.first < v.first; });
+    for (int k = 0; k <= 8; ++k) ps.g8[k] = ps.rec0;
+    for (const auto& kr : keyed) {
+      recs.push_back(kr.second);
+      for (int k = kr.first + 1; k <= 8; ++k) ++ps.g8[k];
     }
     ps.rec1 = (int)recs.size();
   }

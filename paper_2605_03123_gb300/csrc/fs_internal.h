@@ -58,24 +58,31 @@ struct WinStep {
 std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W);
 // Orbit tables of the strings of n electrons in N orbitals for windows of W
 // adjacent orbitals: for each window position a, orbits[off[a] .. off[a+1])
-// hold R_O | c_lo << 16 | m << 24 (sorted by m), and
+// hold R_O | c_lo << 16 | m << 24, grouped by the occupation g of the top
+// three orbitals (orbits of group g start at goff[a * 9 + g], goff[a * 9 + 8]
+// = off[a + 1]) and sorted by m inside a group, and
 // offs[((a * (n+1) + c_lo) << W) + S] is the in-window rank offset.
 void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
-                        std::vector<int>& off, std::vector<uint16_t>& offs);
+                        std::vector<int>& off, std::vector<uint16_t>& offs,
+                        std::vector<int>& goff);
 
 // Device copy of a pass: the subset, the owned slots, the record range.
 struct TPassDev {
   int q[4];
   uint32_t keep;
   int rec0, rec1;
+  int g8[9];  // records of top-3 group g: [g8[g], g8[g + 1])
 };
 // Transition-reduction passes (see tpass_tables_host): a subset of four
 // orbitals q[0] < .. < q[3], the local slots (i*4 + j <-> E_{q_i q_j}) this
-// pass owns, and its orbit records recs[rec0 .. rec1) sorted by m.
+// pass owns, and its orbit records recs[rec0 .. rec1), grouped by the
+// occupation g of the top three orbitals outside the subset (group g at
+// [g8[g], g8[g + 1])) and sorted by m inside a group.
 struct TPass {
   int q[4];
   uint32_t keep;
   int rec0, rec1;
+  int g8[9];
 };
 struct alignas(16) TRecord {
   uint16_t addr[6];  // addresses of O u S, S in ascending local-mask order
@@ -107,6 +114,7 @@ struct Space {
     uint32_t* orbits = nullptr;
     int* off = nullptr;
     uint16_t* offs = nullptr;
+    int* goff = nullptr;  // [npos][9] top-3 group starts
     bool built = false;
   } win[8];
   // transition-reduction passes (reverse mode), built on first use
@@ -241,7 +249,14 @@ struct SweepGeom {
   int d;        // vector length (strings of the rotated spin)
   int nvec;     // number of vectors (strings of the other spin)
   int lgKV;     // log2 of vectors per slab
-  int chunk;    // vector elements held by one CTA of the cluster
+  int chunk;    // vector elements held by one CTA of the cluster (maximum)
+  // cluster rank r holds elements [cb[r], cb[r + 1]) of each vector; with
+  // `blocked`, rank r holds exactly the strings whose occupation of the top
+  // lgcs orbitals reads r (so orbits of windows and subsets clear of those
+  // orbitals stay within one CTA)
+  int cb[9];
+  int lgcs;
+  int blocked;
   const uint32_t* pairs;
   int npp;
   const uint32_t* masks_this;
@@ -267,6 +282,7 @@ struct SweepGeom {
   // window tables of the rotated spin (window kernels only)
   const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
   const int* orb_off;      // [npos + 1] start of each position's list
+  const int* orb_goff;     // [npos][9] top-3 group starts of each list
   const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
   int offs_stride;         // (nocc + 1) << W
 };

@@ -110,8 +110,8 @@ __device__ __forceinline__ void win_offsets(const uint16_t* Fc, int (&e)[sizeof.
 // the slab is rotated in registers by the step's Givens rotations.
 template <typename R, int CS, int NST, int W, int M>
 __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t<R>* const* base,
-                                          size_t st_stride, int chunk, int KV, int kv_eff,
-                                          const WProg<R>& prog, int ga, int gb) {
+                                          size_t st_stride, const int (&cbr)[CS + 1], int KV,
+                                          int kv_eff, const WProg<R>& prog, int ga, int gb) {
   using C = cx_t<R>;
   constexpr int NS = cbinom(W, M);
   const int RO = desc & 0xFFFF, clo = (desc >> 16) & 0xFF;
@@ -124,11 +124,15 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
   for (int k = 0; k < NS; ++k) {
     int e = RO + ad[k];
     if constexpr (CS > 1) {
-      int o = 0;
+      int o = 0, b0 = 0;
 #pragma unroll
-      for (int r = 1; r < CS; ++r) o += e >= r * chunk;
+      for (int r = 1; r < CS; ++r)
+        if (e >= cbr[r]) {
+          o = r;
+          b0 = cbr[r];
+        }
       own[k] = o;
-      ad[k] = (e - o * chunk) * KV;
+      ad[k] = (e - b0) * KV;
     } else {
       ad[k] = e * KV;
     }
@@ -220,8 +224,8 @@ __device__ __forceinline__ void t_flips(int gb, int (&fl)[sizeof...(K)],
 }
 template <typename R, int CS, int M>
 __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base, size_t st_stride,
-                                        int chunk, int KV, int kv_eff, R (&acc)[32],
-                                        uint32_t keep) {
+                                        const int (&cbr)[CS + 1], int KV, int kv_eff,
+                                        R (&acc)[32], uint32_t keep) {
   using C = cx_t<R>;
   constexpr int NS = cbinom(4, M);
   int ad[NS], own[CS > 1 ? NS : 1];
@@ -229,11 +233,15 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
   for (int k = 0; k < NS; ++k) {
     const int e = rc.addr[k];
     if constexpr (CS > 1) {
-      int o = 0;
+      int o = 0, b0 = 0;
 #pragma unroll
-      for (int r = 1; r < CS; ++r) o += e >= r * chunk;
+      for (int r = 1; r < CS; ++r)
+        if (e >= cbr[r]) {
+          o = r;
+          b0 = cbr[r];
+        }
       own[k] = o;
-      ad[k] = (e - o * chunk) * KV;
+      ad[k] = (e - b0) * KV;
     } else {
       ad[k] = e * KV;
     }
@@ -362,8 +370,18 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
   const int KV = 1 << g.lgKV;
   const int v0 = slab * KV;
   const int kv_eff = min(KV, g.nvec - v0);
-  const int e0 = rank * g.chunk;
-  const int nel = max(0, min(g.d - e0, g.chunk));
+  // element ranges of the cluster ranks (registers; rank is runtime)
+  int cbr[CS + 1];
+#pragma unroll
+  for (int r = 0; r <= CS; ++r) cbr[r] = g.cb[r];
+  int e0 = 0, e1 = cbr[CS];
+#pragma unroll
+  for (int r = 0; r < CS; ++r)
+    if (r == rank) {
+      e0 = cbr[r];
+      e1 = cbr[r + 1];
+    }
+  const int nel = max(0, e1 - e0);
   const int tid = threadIdx.x;
   const size_t st_stride = (size_t)g.chunk * KV;  // elements per state
   C* tab = sm + NST * st_stride;                  // cross tables, KV sets
@@ -408,16 +426,22 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         if (kv >= kv_eff) continue;
         uint32_t pr = __ldg(list + t);
         int src = pr & 0xFFFF, dst = pr >> 16;
-        int os = 0, od = 0;
+        int os = 0, od = 0, bs0 = 0, bd0 = 0;
         if constexpr (CS > 1) {
   #pragma unroll
           for (int r = 1; r < CS; ++r) {
-            os += src >= r * g.chunk;
-            od += dst >= r * g.chunk;
+            if (src >= cbr[r]) {
+              os = r;
+              bs0 = cbr[r];
+            }
+            if (dst >= cbr[r]) {
+              od = r;
+              bd0 = cbr[r];
+            }
           }
         }
-        size_t ls = (size_t)(src - os * g.chunk) * KV + kv;
-        size_t ld = (size_t)(dst - od * g.chunk) * KV + kv;
+        size_t ls = (size_t)(src - bs0) * KV + kv;
+        size_t ld = (size_t)(dst - bd0) * KV + kv;
   #pragma unroll
         for (int s = 0; s < NST; ++s) {
           C* ps = base[os] + s * st_stride + ls;
@@ -443,11 +467,11 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       for (int o = o0 + ltid; o < o1; o += HT) {
         const uint32_t desc = __ldg(g.orbits + o);
         switch (desc >> 24) {
-          case 1: win_orbit<R, 1, 1, W, 1>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 2: win_orbit<R, 1, 1, W, 2>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 3: win_orbit<R, 1, 1, W, 3>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 4: if constexpr (W > 4) win_orbit<R, 1, 1, W, 4>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 5: if constexpr (W > 5) win_orbit<R, 1, 1, W, 5>(desc, F, bs, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 1: win_orbit<R, 1, 1, W, 1>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 2: win_orbit<R, 1, 1, W, 2>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 3: win_orbit<R, 1, 1, W, 3>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 4: if constexpr (W > 4) win_orbit<R, 1, 1, W, 4>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 5: if constexpr (W > 5) win_orbit<R, 1, 1, W, 5>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
           default: break;
         }
       }
@@ -460,16 +484,25 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       const int ga = prog.g0[st], gb = prog.g0[st + 1];
       const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
       const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
-      const int per = (o1 - o0 + CS - 1) / CS;
-      const int lo = o0 + rank * per, hi = min(o1, lo + per);
+      int lo, hi;
+      if (CS > 1 && g.blocked && a + W <= g.norb - g.lgcs) {
+        // window clear of the top orbitals: this rank's own orbits
+        const int sh = 3 - g.lgcs;
+        lo = __ldg(g.orb_goff + a * 9 + (rank << sh));
+        hi = __ldg(g.orb_goff + a * 9 + ((rank + 1) << sh));
+      } else {
+        const int per = (o1 - o0 + CS - 1) / CS;
+        lo = o0 + rank * per;
+        hi = min(o1, lo + per);
+      }
       for (int o = lo + tid; o < hi; o += kThreads) {
         const uint32_t desc = __ldg(g.orbits + o);
         switch (desc >> 24) {
-          case 1: win_orbit<R, CS, NST, W, 1>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 2: win_orbit<R, CS, NST, W, 2>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 3: win_orbit<R, CS, NST, W, 3>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 4: if constexpr (W > 4) win_orbit<R, CS, NST, W, 4>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
-          case 5: if constexpr (W > 5) win_orbit<R, CS, NST, W, 5>(desc, F, base, st_stride, g.chunk, KV, kv_eff, prog, ga, gb); break;
+          case 1: win_orbit<R, CS, NST, W, 1>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 2: win_orbit<R, CS, NST, W, 2>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 3: win_orbit<R, CS, NST, W, 3>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 4: if constexpr (W > 4) win_orbit<R, CS, NST, W, 4>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 5: if constexpr (W > 5) win_orbit<R, CS, NST, W, 5>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
           default: break;
         }
       }
@@ -532,26 +565,35 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       for (int i = tid; i < g.npass * 32; i += kThreads) tsm[i] = 0;
       __syncthreads();
       const int lane = tid & 31;
-      for (int P = 0; P < g.npass; ++P) {
-        const TPassDev pd = g.tpass[P];
+      for (int ip = 0; ip < g.npass; ++ip) {
+        const TPassDev pd = g.tpass[ip];
         R acc[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = 0;
-        const int per = (pd.rec1 - pd.rec0 + CS - 1) / CS;
-        const int lo = pd.rec0 + rank * per, hi = min(pd.rec1, lo + per);
+        int lo, hi;
+        if (CS > 1 && g.blocked && pd.q[3] < g.norb - g.lgcs) {
+          // subset clear of the top orbitals: this rank's own records
+          const int sh = 3 - g.lgcs;
+          lo = pd.g8[rank << sh];
+          hi = pd.g8[(rank + 1) << sh];
+        } else {
+          const int per = (pd.rec1 - pd.rec0 + CS - 1) / CS;
+          lo = pd.rec0 + rank * per;
+          hi = min(pd.rec1, lo + per);
+        }
         for (int o = lo + tid; o < hi; o += kThreads) {
           TRecord rc;
           *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
           switch (rc.m) {
-            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
-            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
-            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
-            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, g.chunk, KV, kv_eff, acc, pd.keep); break;
+            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
+            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
+            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
+            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
             default: break;
           }
         }
         const R v = warp_transpose_sum<R>(acc, lane);
-        if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + P * 32 + lane, v);
+        if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + ip * 32 + lane, v);
       }
       __syncthreads();
       for (int i = tid; i < g.npass * 32; i += kThreads) {
@@ -588,16 +630,22 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
             if (t >= cnt) continue;
             const uint32_t sb = (sw[u] >> (t & 31)) & 1u;
             const int src = pr[u] & 0xFFFF, dst = pr[u] >> 16;
-            int os = 0, od = 0;
+            int os = 0, od = 0, bs0 = 0, bd0 = 0;
             if constexpr (CS > 1) {
 #pragma unroll
               for (int r = 1; r < CS; ++r) {
-                os += src >= r * g.chunk;
-                od += dst >= r * g.chunk;
+                if (src >= cbr[r]) {
+                  os = r;
+                  bs0 = cbr[r];
+                }
+                if (dst >= cbr[r]) {
+                  od = r;
+                  bd0 = cbr[r];
+                }
               }
             }
-            const C* ps = base[os] + (size_t)(src - os * g.chunk) * KV;
-            const C* pg = base[od] + st_stride + (size_t)(dst - od * g.chunk) * KV;
+            const C* ps = base[os] + (size_t)(src - bs0) * KV;
+            const C* pg = base[od] + st_stride + (size_t)(dst - bd0) * KV;
             R br = 0, bi = 0;
             for (int kv = 0; kv < kv_eff; ++kv) {
               C a = ps[kv], b = pg[kv];
@@ -706,6 +754,7 @@ static void build_tpass_tables(Space* sp) {
     pd[i].keep = passes[i].keep;
     pd[i].rec0 = passes[i].rec0;
     pd[i].rec1 = passes[i].rec1;
+    for (int j = 0; j < 9; ++j) pd[i].g8[j] = passes[i].g8[j];
   }
   if (!pd.empty()) {
     FS_CUDA(cudaMalloc(&sp->tpass, pd.size() * sizeof(TPassDev)));
@@ -728,10 +777,13 @@ static void build_window_tables(Space* sp, int W) {
   std::vector<uint32_t> orbits;
   std::vector<int> off;
   std::vector<uint16_t> offs;
-  window_tables_host(sp->norb, sp->nocc, W, orbits, off, offs);
+  std::vector<int> goff;
+  window_tables_host(sp->norb, sp->nocc, W, orbits, off, offs, goff);
   FS_CUDA(cudaMalloc(&wt.orbits, std::max<size_t>(orbits.size(), 1) * 4));
   FS_CUDA(cudaMalloc(&wt.off, off.size() * sizeof(int)));
   FS_CUDA(cudaMalloc(&wt.offs, offs.size() * 2));
+  FS_CUDA(cudaMalloc(&wt.goff, goff.size() * sizeof(int)));
+  FS_CUDA(cudaMemcpy(wt.goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!orbits.empty())
     FS_CUDA(cudaMemcpy(wt.orbits, orbits.data(), orbits.size() * 4, cudaMemcpyHostToDevice));
   FS_CUDA(cudaMemcpy(wt.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -822,6 +874,7 @@ static void set_window_geom(SweepGeom& g, Space* sp, int W) {
   const Space::Win& wt = sp->win[W];
   g.orbits = wt.orbits;
   g.orb_off = wt.off;
+  g.orb_goff = wt.goff;
   g.offs = wt.offs;
   g.offs_stride = (sp->nocc + 1) << W;
 }
@@ -866,6 +919,38 @@ static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotPr
   }
   auto prog = make_prog<R>(rp);
   dispatch_cs<R, NST, VJP, 0, 512>(CS, g0, prog, X, nslabs, smem, st);
+}
+
+// Split of each vector over the CS ranks of a cluster.  Preferred: rank r
+// holds the strings whose occupation of the top b = log2(CS) orbitals reads
+// r (a contiguous address range of C(N - b, n - popcount(r)) strings), so
+// that the orbits of windows and subsets clear of those orbitals stay
+// within one CTA; else (the largest such block does not fit) equal chunks.
+template <typename Fits>
+static void set_cluster_layout(SweepGeom& g, const Space* sp, int CS, Fits&& fits) {
+  g.blocked = 0;
+  g.lgcs = 0;
+  g.cb[0] = 0;
+  if (CS > 1) {
+    int b = 0;
+    while ((1 << b) < CS) ++b;
+    int64_t mx = 0;
+    std::vector<int64_t> bs(CS);
+    for (int r = 0; r < CS; ++r) {
+      const int k = sp->nocc - __builtin_popcount(r);
+      bs[r] = (k < 0 || k > sp->norb - b) ? 0 : (int64_t)binom_host(sp->norb - b, k);
+      mx = std::max(mx, bs[r]);
+    }
+    if (sp->norb >= 3 && b <= 3 && fits((int)mx)) {
+      g.blocked = 1;
+      g.lgcs = b;
+      g.chunk = (int)mx;
+      for (int r = 0; r < CS; ++r) g.cb[r + 1] = g.cb[r] + (int)bs[r];
+      return;
+    }
+  }
+  g.chunk = (g.d + CS - 1) / CS;
+  for (int r = 1; r <= CS; ++r) g.cb[r] = std::min(g.d, r * g.chunk);
 }
 
 void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0,
@@ -930,10 +1015,13 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   int lg = 0;
   while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(CS, 2 << lg) <= budget) ++lg;
   g.lgKV = lg;
-  g.chunk = (g.d + CS - 1) / CS;
+  set_cluster_layout(g, sthis, CS, [&](int chunk) {
+    return (size_t)(chunk * csz * nst + tab_per_kv + fixed) + tsum <= maxsm;
+  });
   const int KV = 1 << lg;
   const int nslabs = (g.nvec + KV - 1) / KV;
-  const size_t smem = std::max<size_t>(smem_for(CS, KV), 16);
+  const size_t smem = std::max<size_t>(
+      (size_t)KV * ((size_t)g.chunk * csz * nst + tab_per_kv + fixed) + tsum, 16);
   Space* sw = const_cast<Space*>(sthis);
   if (dtype == FS_C64) {
     if (nst == 1) dispatch_prog<float, 1, false>(sw, CS, g, rp, ph.X, nslabs, smem, two_per_sm, st);
@@ -1006,6 +1094,8 @@ void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* 
   while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(2 << lg) <= budget) ++lg;
   g.lgKV = lg;
   g.chunk = g.d;
+  g.cb[0] = 0;
+  g.cb[1] = g.d;
   out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
   out.smem = smem_for(1 << lg);
   out.prog.resize(wprog_bytes(dtype));

@@ -195,6 +195,7 @@ void free_space(Space* s) {
     cudaFree(w.orbits);
     cudaFree(w.off);
     cudaFree(w.offs);
+    cudaFree(w.goff);
   }
   delete s;
 }

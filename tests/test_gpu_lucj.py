@@ -213,6 +213,33 @@ def test_lucj_vjp_cluster_path_against_oracle(lib):
     assert np.max(np.abs(host(x) - v)) < 1e-12
 
 
+@pytest.fixture(scope="module")
+def n18_cluster_case():
+    """N=18 (9,1): 48620 alpha strings, so the alpha sweeps run on clusters
+    of 2 (complex64 forward), 4 (complex64 reverse, complex128 forward) and
+    8 CTAs (complex128 reverse), each rank holding the strings of one
+    occupation pattern of the top orbitals."""
+    norb, nelec = 18, (9, 1)
+    K, Jaa, Jab, v, c = _small_case(norb, nelec, 1, 14500, False)
+    return (norb, nelec, K, Jaa, Jab, v, c,
+            oracle.lucj_forward(K, Jaa, Jab, norb, nelec, vec=v),
+            oracle.lucj_vjp(K, Jaa, Jab, c, norb, nelec, vec=v))
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_lucj_blocked_clusters_against_oracle(lib, dt, n18_cluster_case):
+    norb, nelec, K, Jaa, Jab, v, c, out, (rK, rJa, rJb, rv) = n18_cluster_case
+    x = dev(v, dt)
+    lib.lucj_forward_(x, K, Jaa, Jab, norb, nelec)
+    assert np.max(np.abs(host(x) - out)) < TOL[dt]
+    cg = dev(c, dt)
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec)
+    tg = 1e-10 if dt == "c128" else 2e-4
+    assert _rel(dK, rK) < tg and _rel(dJa, rJa) < tg and _rel(dJb, rJb) < tg
+    assert np.max(np.abs(host(cg) - rv)) < TOL[dt]
+    assert np.max(np.abs(host(x) - v)) < TOL[dt]
+
+
 def _vdot_rows(a, b, rows=4096):
     """<a, b> over row blocks (one cuBLAS dot is limited to 2^31 elements)."""
     return sum(complex(torch.vdot(a[i:i + rows].flatten(), b[i:i + rows].flatten()).item())
