@@ -173,11 +173,6 @@ std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W) {
   return steps;
 }
 
-// For the window [a, a+W): every outside configuration O with
-// m = n - |O| in 1 .. W-1 is one orbit.  With c_lo = |O below a|, the address
-// of O u S (S inside the window) is R_O + F[a][c_lo][S], where R_O sums
-// C(o_k, k+1) over O's orbitals with their index k in the full string and F
-// sums the same terms over S's orbitals (combinatorial-number-system rank).
 // Top-3 group of a configuration: the occupation of orbitals N-1, N-2, N-3
 // read as a 3-bit number (the strings of one group form a contiguous range
 // of addresses, since addresses follow the integer order of the masks).
@@ -185,13 +180,18 @@ static inline int top3_group(uint32_t mask, int N) {
   return N >= 3 ? (int)((mask >> (N - 3)) & 7u) : 0;
 }
 
+// For the window [a, a+W): every outside configuration O with
+// m = n - |O| in 1 .. W-1 is one orbit.  With c_lo = |O below a|, the address
+// of O u S (S inside the window) is R_O + F[a][c_lo][S], where R_O sums
+// C(o_k, k+1) over O's orbitals with their index k in the full string and F
+// sums the same terms over S's orbitals (combinatorial-number-system rank).
 void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
                         std::vector<int>& off, std::vector<uint16_t>& offs,
-                        std::vector<int>& goff) {
+                        std::vector<uint8_t>& okey) {
   const int npos = N - W + 1;
   orbits.clear();
+  okey.clear();
   off.assign(npos + 1, 0);
-  goff.assign((size_t)npos * 9, 0);
   offs.assign((size_t)npos * (n + 1) << W, 0);
   auto C = [](int a, int b) -> uint64_t {
     if (b < 0 || b > a) return 0;
@@ -201,7 +201,6 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
   };
   for (int a = 0; a < npos; ++a) {
     off[a] = (int)orbits.size();
-    std::vector<std::pair<int, uint32_t>> keyed;  // (top-3 group, descriptor)
     std::vector<int> out;
     for (int p = 0; p < N; ++p)
       if (p < a || p >= a + W) out.push_back(p);
@@ -227,25 +226,15 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
             }
             ++k;
           }
-        keyed.emplace_back(top3_group(omask, N),
-                           (uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
+        orbits.push_back((uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
+        okey.push_back((uint8_t)top3_group(omask, N));
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), r = x + c;
         x = (((r ^ x) >> 2) / c) | r;
         if (x >> no) break;
       }
     }
-    // grouped by the occupation of the top three orbitals (for windows
-    // clear of them, every string of an orbit lies in that group's address
-    // range), sorted by m inside a group
-    std::stable_sort(keyed.begin(), keyed.end(),
-                     [](const auto& u, const auto& v) { return u.first < v.first; });
-    int* go = &goff[(size_t)a * 9];
-    for (int k = 0; k <= 8; ++k) go[k] = off[a];
-    for (const auto& kd : keyed) {
-      orbits.push_back(kd.second);
-      for (int k = kd.first + 1; k <= 8; ++k) ++go[k];
-    }
+
     for (int clo = 0; clo <= n; ++clo)
       for (int S = 0; S < (1 << W); ++S) {
         uint64_t f = 0;
@@ -270,9 +259,10 @@ namespace fs {
 // C(4, m) subsets S of Q (ascending local masks) and the parities of the
 // numbers of O-orbitals in the three gaps of Q.
 void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
-                       std::vector<TRecord>& recs) {
+                       std::vector<TRecord>& recs, std::vector<uint8_t>& rkey) {
   passes.clear();
   recs.clear();
+  rkey.clear();
   if (N < 4) return;
   // N = 16: the lines of the affine plane over GF(4), 20 subsets covering
   // every pair exactly once (point (x, y) <-> orbital 4x + y; GF(4) addition
@@ -379,7 +369,6 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
   };
   for (auto& ps : passes) {
     ps.rec0 = (int)recs.size();
-    std::vector<std::pair<int, TRecord>> keyed;  // (top-3 group of O, record)
     uint32_t qmask = 0;
     for (int i = 0; i < 4; ++i) qmask |= 1u << ps.q[i];
     std::vector<int> out;
@@ -411,23 +400,54 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
           g |= (uint8_t)(acc << (j + 1));  // bit j+1: parity of O before q_{j+1}
         }
         r.gbits = g;
-        keyed.emplace_back(top3_group(omask, N), r);
+        recs.push_back(r);
+        rkey.push_back((uint8_t)top3_group(omask, N));
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), rr = x + c;
         x = (((rr ^ x) >> 2) / c) | rr;
         if (x >> no) break;
       }
     }
-    // grouped by the top-3 occupation of O, sorted by m inside a group
-    std::stable_sort(keyed.begin(), keyed.end(),
-                     [](const auto& u, const auto& v) { return u.first < v.first; });
-    for (int k = 0; k <= 8; ++k) ps.g8[k] = ps.rec0;
-    for (const auto& kr : keyed) {
-      recs.push_back(kr.second);
-      for (int k = kr.first + 1; k <= 8; ++k) ++ps.g8[k];
-    }
     ps.rec1 = (int)recs.size();
   }
+}
+
+// Regrouping of an item list for clusters of 2^b CTAs: within each segment
+// [seg[i], seg[i + 1]) the items are stably reordered by their top-b group
+// key >> (3 - b) (keeping the m order inside a group); gofs[i * 9 + r] is the
+// start of group r of segment i (r = 0 .. 2^b, the last entry the segment
+// end).
+template <typename T>
+static void regroup(const std::vector<T>& items, const std::vector<uint8_t>& key,
+                    const std::vector<int>& seg, int b, std::vector<T>& out,
+                    std::vector<int>& gofs) {
+  const int ns = (int)seg.size() - 1, G = 1 << b;
+  out.clear();
+  out.reserve(items.size());
+  gofs.assign((size_t)std::max(ns, 0) * 9, 0);
+  for (int i = 0; i < ns; ++i) {
+    for (int r = 0; r < G; ++r) {
+      gofs[(size_t)i * 9 + r] = (int)out.size();
+      for (int k = seg[i]; k < seg[i + 1]; ++k)
+        if ((key[k] >> (3 - b)) == r) out.push_back(items[k]);
+    }
+    for (int r = G; r <= 8; ++r) gofs[(size_t)i * 9 + r] = (int)out.size();
+  }
+}
+
+void window_groups_host(const std::vector<uint32_t>& orbits, const std::vector<int>& off,
+                        const std::vector<uint8_t>& okey, int b, std::vector<uint32_t>& gorb,
+                        std::vector<int>& goff) {
+  regroup(orbits, okey, off, b, gorb, goff);
+}
+
+void tpass_groups_host(const std::vector<TPass>& passes, const std::vector<TRecord>& recs,
+                       const std::vector<uint8_t>& rkey, int b, std::vector<TRecord>& grec,
+                       std::vector<int>& goff) {
+  std::vector<int> seg;
+  for (const auto& p : passes) seg.push_back(p.rec0);
+  seg.push_back(passes.empty() ? 0 : passes.back().rec1);
+  regroup(recs, rkey, seg, b, grec, goff);
 }
 
 }  // namespace fs

@@ -58,12 +58,18 @@ struct WinStep {
 std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W);
 // Orbit tables of the strings of n electrons in N orbitals for windows of W
 // adjacent orbitals: for each window position a, orbits[off[a] .. off[a+1])
-// hold R_O | c_lo << 16 | m << 24, grouped by the occupation g of the top
-// three orbitals (orbits of group g start at goff[a * 9 + g], goff[a * 9 + 8]
-// = off[a + 1]) and sorted by m inside a group, and
-// offs[((a * (n+1) + c_lo) << W) + S] is the in-window rank offset.
+// hold R_O | c_lo << 16 | m << 24 sorted by m, okey[i] is the occupation of
+// the top three orbitals in orbit i's outside configuration (a 3-bit
+// number), and offs[((a * (n+1) + c_lo) << W) + S] is the in-window rank
+// offset.
 void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
                         std::vector<int>& off, std::vector<uint16_t>& offs,
+                        std::vector<uint8_t>& okey);
+// The orbits regrouped for clusters of 2^b CTAs: per window position a,
+// group r (occupation of the top b orbitals, the strings of cluster rank r)
+// at gorb[goff[a * 9 + r] .. goff[a * 9 + r + 1]), sorted by m inside.
+void window_groups_host(const std::vector<uint32_t>& orbits, const std::vector<int>& off,
+                        const std::vector<uint8_t>& okey, int b, std::vector<uint32_t>& gorb,
                         std::vector<int>& goff);
 
 // Device copy of a pass: the subset, the owned slots, the record range.
@@ -71,18 +77,14 @@ struct TPassDev {
   int q[4];
   uint32_t keep;
   int rec0, rec1;
-  int g8[9];  // records of top-3 group g: [g8[g], g8[g + 1])
 };
 // Transition-reduction passes (see tpass_tables_host): a subset of four
 // orbitals q[0] < .. < q[3], the local slots (i*4 + j <-> E_{q_i q_j}) this
-// pass owns, and its orbit records recs[rec0 .. rec1), grouped by the
-// occupation g of the top three orbitals outside the subset (group g at
-// [g8[g], g8[g + 1])) and sorted by m inside a group.
+// pass owns, and its orbit records recs[rec0 .. rec1) sorted by m.
 struct TPass {
   int q[4];
   uint32_t keep;
   int rec0, rec1;
-  int g8[9];
 };
 struct alignas(16) TRecord {
   uint16_t addr[6];  // addresses of O u S, S in ascending local-mask order
@@ -90,8 +92,15 @@ struct alignas(16) TRecord {
   uint8_t gbits;     // bit j: parity of |O| between q_0 and q_j (j = 1..3)
   uint16_t pad;
 };
+// rkey[i]: occupation of the top three orbitals in record i's configuration
+// outside the subset (a 3-bit number).
 void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
-                       std::vector<TRecord>& recs);
+                       std::vector<TRecord>& recs, std::vector<uint8_t>& rkey);
+// The records regrouped for clusters of 2^b CTAs: per pass i, group r at
+// grec[goff[i * 9 + r] .. goff[i * 9 + r + 1]), sorted by m inside.
+void tpass_groups_host(const std::vector<TPass>& passes, const std::vector<TRecord>& recs,
+                       const std::vector<uint8_t>& rkey, int b, std::vector<TRecord>& grec,
+                       std::vector<int>& goff);
 
 // ------------------------------------------------------ device tables
 // Per-sector-spin tables: strings of `nocc` electrons in `norb` orbitals.
@@ -114,14 +123,26 @@ struct Space {
     uint32_t* orbits = nullptr;
     int* off = nullptr;
     uint16_t* offs = nullptr;
-    int* goff = nullptr;  // [npos][9] top-3 group starts
     bool built = false;
+    // regrouped for clusters of 2^b CTAs (index b), built on first use from
+    // the host copies
+    uint32_t* gorb[4] = {};
+    int* goff[4] = {};
+    std::vector<uint32_t> orb_h;
+    std::vector<int> off_h;
+    std::vector<uint8_t> okey_h;
   } win[8];
-  // transition-reduction passes (reverse mode), built on first use
+  // transition-reduction passes (reverse mode), built on first use, and the
+  // records regrouped for clusters of 2^b CTAs
   struct TPassDev* tpass = nullptr;
   struct TRecord* trec = nullptr;
   int npass = 0;
   bool tbuilt = false;
+  struct TRecord* tgrec[4] = {};
+  int* tgoff[4] = {};
+  std::vector<TPass> tpass_h;
+  std::vector<TRecord> trec_h;
+  std::vector<uint8_t> rkey_h;
 };
 
 struct Scratch {
@@ -282,7 +303,13 @@ struct SweepGeom {
   // window tables of the rotated spin (window kernels only)
   const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
   const int* orb_off;      // [npos + 1] start of each position's list
-  const int* orb_goff;     // [npos][9] top-3 group starts of each list
+  // blocked clusters: orbits regrouped by cluster rank, rank r's orbits of
+  // position a at orb_grp[orb_goff[a * 9 + r] .. orb_goff[a * 9 + r + 1]);
+  // records likewise, rank r's of pass i at trec_grp[tgoff[i * 9 + r] ..)
+  const uint32_t* orb_grp;
+  const int* orb_goff;
+  const TRecord* trec_grp;
+  const int* tgoff;
   const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
   int offs_stride;         // (nocc + 1) << W
 };

@@ -346,6 +346,18 @@ __device__ void build_cross_tables(const SweepGeom& g, const Mat& X, int v0, int
   __syncthreads();
 }
 
+// Asynchronous copy of one complex element from global to shared memory
+// (8 bytes for complex64, 16 for complex128; both addresses aligned to the
+// element size).
+__device__ __forceinline__ void cp_async_elem(cx_t<float>* dst, const cx_t<float>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(cx_t<double>* dst, const cx_t<double>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <typename R>
 __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
   if (!p) return mk<R>(1, 0);
@@ -363,7 +375,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
                                            const int slab, const int rank,
                                            unsigned char* smraw) {
   static_assert(!VJP || NST == 2, "reverse mode carries two states");
-  static_assert(!SPLIT || (NST == 2 && CS == 1 && W > 0), "split mode: two states, one CTA");
+  static_assert(!SPLIT || (NST == 2 && W > 0), "split mode: two states, window sweeps");
   constexpr int kThreads = NT;
   using C = cx_t<R>;
   C* sm = reinterpret_cast<C*>(smraw);
@@ -395,22 +407,26 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
     base[0] = sm;
   }
 
-  // ---- load this CTA's part of the slab
+  // ---- load this CTA's part of the slab: asynchronous element copies
+  //      straight into shared memory (no register round trip, so the strided
+  //      column gathers of an alpha slab all overlap)
   for (int s = 0; s < NST; ++s) {
     const C* gs = reinterpret_cast<const C*>(g.st[s]);
     C* ss = sm + s * st_stride;
     if (g.dir == 1) {
       for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
         int kv = idx / nel, el = idx - kv * nel;
-        ss[(size_t)el * KV + kv] = gs[(int64_t)(v0 + kv) * g.d_b + e0 + el];
+        cp_async_elem(ss + (size_t)el * KV + kv, gs + (int64_t)(v0 + kv) * g.d_b + e0 + el);
       }
     } else {
       for (int idx = tid; idx < (nel << g.lgKV); idx += kThreads) {
         int el = idx >> g.lgKV, kv = idx & (KV - 1);
-        if (kv < kv_eff) ss[(size_t)el * KV + kv] = gs[(int64_t)(e0 + el) * g.d_b + v0 + kv];
+        if (kv < kv_eff)
+          cp_async_elem(ss + (size_t)el * KV + kv, gs + (int64_t)(e0 + el) * g.d_b + v0 + kv);
       }
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
 
   // ---- Givens rotations, in program order
@@ -455,29 +471,50 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     }
   } else if constexpr (SPLIT) {
-    // half h rotates state h; its threads meet on named barrier 1 + h
+    // half h of every CTA rotates state h (one state per thread: the wider
+    // single-state window fits the registers).  In one CTA each half meets
+    // on its own named barrier 1 + h; in a cluster every step ends with the
+    // cluster barrier.
     constexpr int HT = NT / 2;
     const int half = tid / HT, ltid = tid - half * HT;
-    C* bs[1] = {sm + half * st_stride};
+    C* bs[CS];
+#pragma unroll
+    for (int r = 0; r < CS; ++r) bs[r] = base[r] + half * st_stride;
     for (int st = 0; st < prog.nsteps; ++st) {
       const int a = prog.a[st];
       const int ga = prog.g0[st], gb = prog.g0[st + 1];
       const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
       const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
-      for (int o = o0 + ltid; o < o1; o += HT) {
-        const uint32_t desc = __ldg(g.orbits + o);
+      int lo = o0, hi = o1;
+      const uint32_t* olist = g.orbits;
+      if constexpr (CS > 1) {
+        if (g.blocked && a + W <= g.norb - g.lgcs) {
+          olist = g.orb_grp;
+          lo = __ldg(g.orb_goff + a * 9 + rank);
+          hi = __ldg(g.orb_goff + a * 9 + rank + 1);
+        } else {
+          const int per = (o1 - o0 + CS - 1) / CS;
+          lo = o0 + rank * per;
+          hi = min(o1, lo + per);
+        }
+      }
+      for (int o = lo + ltid; o < hi; o += HT) {
+        const uint32_t desc = __ldg(olist + o);
         switch (desc >> 24) {
-          case 1: win_orbit<R, 1, 1, W, 1>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
-          case 2: win_orbit<R, 1, 1, W, 2>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
-          case 3: win_orbit<R, 1, 1, W, 3>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
-          case 4: if constexpr (W > 4) win_orbit<R, 1, 1, W, 4>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
-          case 5: if constexpr (W > 5) win_orbit<R, 1, 1, W, 5>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 1: win_orbit<R, CS, 1, W, 1>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 2: win_orbit<R, CS, 1, W, 2>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 3: win_orbit<R, CS, 1, W, 3>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 4: if constexpr (W > 4) win_orbit<R, CS, 1, W, 4>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
+          case 5: if constexpr (W > 5) win_orbit<R, CS, 1, W, 5>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
           default: break;
         }
       }
-      asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(HT) : "memory");
+      if constexpr (CS > 1)
+        cg::this_cluster().sync();
+      else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(HT) : "memory");
     }
-    __syncthreads();
+    if constexpr (CS == 1) __syncthreads();
   } else {
     for (int st = 0; st < prog.nsteps; ++st) {
       const int a = prog.a[st];
@@ -485,18 +522,19 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
       const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
       int lo, hi;
+      const uint32_t* olist = g.orbits;
       if (CS > 1 && g.blocked && a + W <= g.norb - g.lgcs) {
         // window clear of the top orbitals: this rank's own orbits
-        const int sh = 3 - g.lgcs;
-        lo = __ldg(g.orb_goff + a * 9 + (rank << sh));
-        hi = __ldg(g.orb_goff + a * 9 + ((rank + 1) << sh));
+        olist = g.orb_grp;
+        lo = __ldg(g.orb_goff + a * 9 + rank);
+        hi = __ldg(g.orb_goff + a * 9 + rank + 1);
       } else {
         const int per = (o1 - o0 + CS - 1) / CS;
         lo = o0 + rank * per;
         hi = min(o1, lo + per);
       }
       for (int o = lo + tid; o < hi; o += kThreads) {
-        const uint32_t desc = __ldg(g.orbits + o);
+        const uint32_t desc = __ldg(olist + o);
         switch (desc >> 24) {
           case 1: win_orbit<R, CS, NST, W, 1>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
           case 2: win_orbit<R, CS, NST, W, 2>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
@@ -571,11 +609,12 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = 0;
         int lo, hi;
+        const TRecord* rlist = g.trec;
         if (CS > 1 && g.blocked && pd.q[3] < g.norb - g.lgcs) {
           // subset clear of the top orbitals: this rank's own records
-          const int sh = 3 - g.lgcs;
-          lo = pd.g8[rank << sh];
-          hi = pd.g8[(rank + 1) << sh];
+          rlist = g.trec_grp;
+          lo = __ldg(g.tgoff + ip * 9 + rank);
+          hi = __ldg(g.tgoff + ip * 9 + rank + 1);
         } else {
           const int per = (pd.rec1 - pd.rec0 + CS - 1) / CS;
           lo = pd.rec0 + rank * per;
@@ -583,7 +622,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         }
         for (int o = lo + tid; o < hi; o += kThreads) {
           TRecord rc;
-          *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
+          *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(rlist + o));
           switch (rc.m) {
             case 1: t_orbit<R, CS, 1>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
             case 2: t_orbit<R, CS, 2>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
@@ -745,16 +784,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 // tpass_tables_host).
 static void build_tpass_tables(Space* sp) {
   if (sp->tbuilt) return;
-  std::vector<TPass> passes;
-  std::vector<TRecord> recs;
-  tpass_tables_host(sp->norb, sp->nocc, passes, recs);
+  std::vector<TPass>& passes = sp->tpass_h;
+  std::vector<TRecord>& recs = sp->trec_h;
+  tpass_tables_host(sp->norb, sp->nocc, passes, recs, sp->rkey_h);
   std::vector<TPassDev> pd(passes.size());
   for (size_t i = 0; i < passes.size(); ++i) {
     for (int j = 0; j < 4; ++j) pd[i].q[j] = passes[i].q[j];
     pd[i].keep = passes[i].keep;
     pd[i].rec0 = passes[i].rec0;
     pd[i].rec1 = passes[i].rec1;
-    for (int j = 0; j < 9; ++j) pd[i].g8[j] = passes[i].g8[j];
   }
   if (!pd.empty()) {
     FS_CUDA(cudaMalloc(&sp->tpass, pd.size() * sizeof(TPassDev)));
@@ -774,21 +812,50 @@ static void build_tpass_tables(Space* sp) {
 static void build_window_tables(Space* sp, int W) {
   Space::Win& wt = sp->win[W];
   if (wt.built) return;
-  std::vector<uint32_t> orbits;
-  std::vector<int> off;
+  std::vector<uint32_t>& orbits = wt.orb_h;
+  std::vector<int>& off = wt.off_h;
   std::vector<uint16_t> offs;
-  std::vector<int> goff;
-  window_tables_host(sp->norb, sp->nocc, W, orbits, off, offs, goff);
+  window_tables_host(sp->norb, sp->nocc, W, orbits, off, offs, wt.okey_h);
   FS_CUDA(cudaMalloc(&wt.orbits, std::max<size_t>(orbits.size(), 1) * 4));
   FS_CUDA(cudaMalloc(&wt.off, off.size() * sizeof(int)));
   FS_CUDA(cudaMalloc(&wt.offs, offs.size() * 2));
-  FS_CUDA(cudaMalloc(&wt.goff, goff.size() * sizeof(int)));
-  FS_CUDA(cudaMemcpy(wt.goff, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!orbits.empty())
     FS_CUDA(cudaMemcpy(wt.orbits, orbits.data(), orbits.size() * 4, cudaMemcpyHostToDevice));
   FS_CUDA(cudaMemcpy(wt.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
   FS_CUDA(cudaMemcpy(wt.offs, offs.data(), offs.size() * 2, cudaMemcpyHostToDevice));
   wt.built = true;
+}
+
+// Orbit and record lists regrouped by cluster rank for clusters of 2^b CTAs
+// with the blocked layout (built once per space and b).
+static void build_window_groups(Space* sp, int W, int b) {
+  Space::Win& wt = sp->win[W];
+  if (wt.gorb[b]) return;
+  std::vector<uint32_t> gorb;
+  std::vector<int> goff;
+  window_groups_host(wt.orb_h, wt.off_h, wt.okey_h, b, gorb, goff);
+  FS_CUDA(cudaMalloc(&wt.gorb[b], std::max<size_t>(gorb.size(), 1) * 4));
+  FS_CUDA(cudaMalloc(&wt.goff[b], std::max<size_t>(goff.size(), 1) * sizeof(int)));
+  if (!gorb.empty())
+    FS_CUDA(cudaMemcpy(wt.gorb[b], gorb.data(), gorb.size() * 4, cudaMemcpyHostToDevice));
+  if (!goff.empty())
+    FS_CUDA(cudaMemcpy(wt.goff[b], goff.data(), goff.size() * sizeof(int),
+                       cudaMemcpyHostToDevice));
+}
+
+static void build_tpass_groups(Space* sp, int b) {
+  if (sp->tgrec[b] || sp->tpass_h.empty()) return;
+  std::vector<TRecord> grec;
+  std::vector<int> goff;
+  tpass_groups_host(sp->tpass_h, sp->trec_h, sp->rkey_h, b, grec, goff);
+  FS_CUDA(cudaMalloc(&sp->tgrec[b], std::max<size_t>(grec.size(), 1) * sizeof(TRecord)));
+  FS_CUDA(cudaMalloc(&sp->tgoff[b], std::max<size_t>(goff.size(), 1) * sizeof(int)));
+  if (!grec.empty())
+    FS_CUDA(cudaMemcpy(sp->tgrec[b], grec.data(), grec.size() * sizeof(TRecord),
+                       cudaMemcpyHostToDevice));
+  if (!goff.empty())
+    FS_CUDA(cudaMemcpy(sp->tgoff[b], goff.data(), goff.size() * sizeof(int),
+                       cudaMemcpyHostToDevice));
 }
 
 template <typename R>
@@ -850,14 +917,14 @@ static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
   FS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, prog, X));
 }
 
-template <typename R, int NST, bool VJP, int W, int NT, typename P>
+template <typename R, int NST, bool VJP, int W, int NT, typename P, bool SPLIT = false>
 static void dispatch_cs(int CS, const SweepGeom& g, const P& prog, const Mat& X,
                         int nslabs, size_t smem, cudaStream_t st) {
   switch (CS) {
-    case 1: launch_sweep_t<R, 1, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
-    case 2: launch_sweep_t<R, 2, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
-    case 4: launch_sweep_t<R, 4, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
-    case 8: launch_sweep_t<R, 8, NST, VJP, W, NT, false>(g, prog, X, nslabs, smem, st); break;
+    case 1: launch_sweep_t<R, 1, NST, VJP, W, NT, SPLIT>(g, prog, X, nslabs, smem, st); break;
+    case 2: launch_sweep_t<R, 2, NST, VJP, W, NT, SPLIT>(g, prog, X, nslabs, smem, st); break;
+    case 4: launch_sweep_t<R, 4, NST, VJP, W, NT, SPLIT>(g, prog, X, nslabs, smem, st); break;
+    case 8: launch_sweep_t<R, 8, NST, VJP, W, NT, SPLIT>(g, prog, X, nslabs, smem, st); break;
     default: FS_REQUIRE(false, FS_ERR_UNSUPPORTED, "cluster size out of range");
   }
 }
@@ -874,7 +941,11 @@ static void set_window_geom(SweepGeom& g, Space* sp, int W) {
   const Space::Win& wt = sp->win[W];
   g.orbits = wt.orbits;
   g.orb_off = wt.off;
-  g.orb_goff = wt.goff;
+  if (g.blocked) {
+    build_window_groups(sp, W, g.lgcs);
+    g.orb_grp = wt.gorb[g.lgcs];
+    g.orb_goff = wt.goff[g.lgcs];
+  }
   g.offs = wt.offs;
   g.offs_stride = (sp->nocc + 1) << W;
 }
@@ -882,7 +953,9 @@ static void set_window_geom(SweepGeom& g, Space* sp, int W) {
 // Kernel choice: window sweeps when the orbitals allow a window; forward
 // sweeps on 256 threads when a slab is small enough for two CTAs per SM
 // (their window-step barriers then overlap), else 512; reverse sweeps in
-// split mode (one half-CTA per state) unless the vector spans a cluster.
+// split mode (one half-CTA per state) unless the vector spans a cluster (in a
+// cluster the joint form measured faster: the split form gains little when
+// every step ends on the cluster barrier).
 template <typename R, int NST, bool VJP>
 static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotProgram& rp,
                           const Mat& X, int nslabs, size_t smem, bool two_per_sm,
@@ -1018,6 +1091,11 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   set_cluster_layout(g, sthis, CS, [&](int chunk) {
     return (size_t)(chunk * csz * nst + tab_per_kv + fixed) + tsum <= maxsm;
   });
+  if (g.blocked && g.npass > 0) {
+    build_tpass_groups(const_cast<Space*>(sthis), g.lgcs);
+    g.trec_grp = sthis->tgrec[g.lgcs];
+    g.tgoff = sthis->tgoff[g.lgcs];
+  }
   const int KV = 1 << lg;
   const int nslabs = (g.nvec + KV - 1) / KV;
   const size_t smem = std::max<size_t>(

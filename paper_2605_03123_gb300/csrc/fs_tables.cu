@@ -191,11 +191,18 @@ void free_space(Space* s) {
   cudaFree(s->xcount);
   cudaFree(s->tpass);
   cudaFree(s->trec);
+  for (int b = 0; b < 4; ++b) {
+    cudaFree(s->tgrec[b]);
+    cudaFree(s->tgoff[b]);
+  }
   for (auto& w : s->win) {
     cudaFree(w.orbits);
     cudaFree(w.off);
     cudaFree(w.offs);
-    cudaFree(w.goff);
+    for (int b = 0; b < 4; ++b) {
+      cudaFree(w.gorb[b]);
+      cudaFree(w.goff[b]);
+    }
   }
   delete s;
 }
