@@ -335,6 +335,9 @@ def run_gpu(args):
             out["batch"] = run_batch(args, ctx)
         if args.largest:
             out["largest"] = run_largest(args, ctx)
+        if args.extras:
+            out["dc_phase"] = run_dc_phase(args, ctx)
+            out["small_rotation"] = run_small_rotation(args, ctx)
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -496,6 +499,62 @@ def run_largest(args, ctx):
             "c64_vs_c128_fwd_max_abs": err}
 
 
+def run_dc_phase(args, ctx):
+    """Standalone diagonal-Coulomb evolution at N=16 (8,8): one streaming
+    pass over the state (algorithmic bytes 2S).  complex64 takes the
+    tensor-core cross term (mma.sync bf16 pieces), complex128 the CUDA-core
+    subset-sum tables."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    peak, kind = peaks()
+    g = inputs.rng(2100)
+    Ja, Jb = inputs.random_symmetric(16, 0.5, g), inputs.random_symmetric(16, 0.5, g)
+    out = {"workload": "diag_coulomb_norb16_nelec8_8_t0.3", "peak_gbs": peak,
+           "peak_source": kind}
+    for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        v = inputs.device_state(16, (8, 8), 7, dt)
+        S = v.numel() * v.element_size()
+        f = lambda: fsgpu.apply_diag_coulomb_evolution_(v, Ja, Jb, 0.3, 16, (8, 8), ctx=ctx)
+        for _ in range(3):
+            f()
+        ms = _timed(lambda: [f() for _ in range(5)]) / 5
+        gbs = 2 * S / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": 2 * S, "achieved_gbs": gbs,
+                     "frac": gbs / peak}
+        del v
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_small_rotation(args, ctx):
+    """Orbital rotation of small sectors by Givens sweeps and by dense
+    minor-matrix GEMMs, and the method the autotuner keeps."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    res = {}
+    for N in (8, 10, 12):
+        ne = (N // 2, N // 2)
+        g = inputs.rng(2200 + N)
+        U = inputs.haar_unitary(N, g)
+        row = {}
+        for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+            v = inputs.device_state(N, ne, 8, dt)
+            t = {}
+            for path, pn in ((fsgpu.FS_ROT_GIVENS, "givens"), (fsgpu.FS_ROT_MINORS, "minors")):
+                ctx.set_rotation_path(path)
+                f = lambda: fsgpu.apply_orbital_rotation_(v, U, N, ne, ctx=ctx)
+                for _ in range(3):
+                    f()
+                t[pn] = _timed(lambda: [f() for _ in range(10)]) / 10
+            ctx.set_rotation_path(fsgpu.FS_ROT_AUTO)
+            fsgpu.apply_orbital_rotation_(v, U, N, ne, ctx=ctx)
+            t["auto"] = _timed(lambda: [fsgpu.apply_orbital_rotation_(v, U, N, ne, ctx=ctx)
+                                        for _ in range(10)]) / 10
+            row[name] = {k: round(x, 4) for k, x in t.items()}
+        res["norb%d" % N] = row
+    return {"unit": "ms per rotation", **res}
+
+
 # ------------------------------------------------------------------ oracle
 def cpu_baseline(w, budget_s=None):
     """The oracle, as it stands, on a bounded sample of the workload, scaled
@@ -585,6 +644,9 @@ def main():
                     help="plain-path sample of the batch: every k-th circuit")
     ap.add_argument("--largest", type=int, default=1,
                     help="timed steps of the N=18 (9,9) state (0 skips it)")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="standalone diagonal-Coulomb pass and small-sector rotation "
+                         "methods (0 skips them)")
     ap.add_argument("--norb", type=int, default=0,
                     help="profiling only: another sector size instead of the N=16 workload")
     ap.add_argument("--nalpha", type=int, default=0)

@@ -81,6 +81,83 @@ __global__ void k_hf_batch(const BVec* jobs, int njobs, int64_t total) {
   }
 }
 
+// Slater start of a circuit from Hartree-Fock (§2.4): the first merged
+// rotation R_0 maps HF to a Slater determinant, psi = a b^T with
+// a[I] = det(R_0[I, {0..n_a-1}]) (likewise b); one job per (circuit, spin).
+struct BSl {
+  const uint32_t* masks;
+  double2* out;
+  const CMat* R;  // device
+  int64_t item0;
+  int norb, n;
+};
+__global__ void k_slater_batch(const BSl* jobs, int njobs, int64_t total) {
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const BSl& J = jobs[find_job(jobs, njobs, it)];
+    const int64_t e = it - J.item0;
+    J.out[e] = slater_minor(J.masks[e], J.norb, J.n, J.R->v);
+  }
+}
+
+// psi = a b^T followed by the first diagonal-Coulomb gate: one CTA per
+// (circuit, alpha row); the row's cross angles w[q] = sum_{p in I_a} X[p][q]
+// become 8-bit subset tables, the same-spin parts arrive as string factors.
+struct BSd {
+  void* vec;
+  const double2* va;
+  const double2* vb;
+  const void* ea_a;
+  const void* ea_b;
+  const Mat* X;  // device: -J_ab of the first gate
+  const uint32_t* ma;
+  const uint32_t* mb;
+  int64_t db;
+  int norb;
+  int64_t item0;  // alpha rows
+};
+template <typename R>
+__global__ void __launch_bounds__(256) k_slater_dc_batch(const BSd* jobs, int njobs,
+                                                         int64_t total) {
+  using C = cx_t<R>;
+  __shared__ double w[32];
+  __shared__ C tab[4 * 256];
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    const BSd& J = jobs[find_job(jobs, njobs, it)];
+    const int64_t i = it - J.item0;
+    const uint32_t mi = J.ma[i];
+    const int N = J.norb, nch = (N + 7) / 8;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      double sum = 0;
+      for (uint32_t m = mi; m; m &= m - 1) sum += J.X->v[(__ffs(m) - 1) * N + q];
+      w[q] = sum;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nch * 256; idx += blockDim.x) {
+      const int c = idx >> 8;
+      double sum = 0;
+      for (int v = idx & 255; v; v &= v - 1) {
+        const int x = 8 * c + __ffs(v) - 1;
+        if (x < N) sum += w[x];
+      }
+      tab[idx] = expi<R>(sum);
+    }
+    __syncthreads();
+    const double2 a = J.va[i];
+    const C ea = reinterpret_cast<const C*>(J.ea_a)[i];
+    C* row = reinterpret_cast<C*>(J.vec) + i * J.db;
+    for (int64_t j = threadIdx.x; j < J.db; j += blockDim.x) {
+      const double2 b = J.vb[j];
+      C f = mk<R>((R)(a.x * b.x - a.y * b.y), (R)(a.x * b.y + a.y * b.x));
+      f = cmul<R>(f, cmul<R>(ea, reinterpret_cast<const C*>(J.ea_b)[j]));
+      const uint32_t m = __ldg(J.mb + j);
+      for (int c = 0; c < nch; ++c) f = cmul<R>(f, tab[c * 256 + ((m >> (8 * c)) & 255)]);
+      row[j] = f;
+    }
+    __syncthreads();
+  }
+}
+
 // Gradient of one diagonal-Coulomb gate per job from W (as fs_reduce.cu):
 // rows give Occ_a^T W Occ_b and the alpha part of dJ_aa, columns the beta
 // part.
@@ -219,12 +296,16 @@ struct Circuit {
   // device pointers (scratch arena)
   void *ea_a, *ea_b, *ea_o, *e2_a, *e2_b, *W;
   double *T, *dJ, *colsum;
+  double2 *sl_a, *sl_b;     // Slater start vectors (from Hartree-Fock only)
   size_t jaa_off, xab_off;  // image offsets: J_aa (R x N x N), X mats (2R Mat)
+  size_t r0_off;            // image offset of R_0 (CMat, from Hartree-Fock only)
+  bool hf() const { return op->from_hf != 0; }
 };
 
 // A stage: kernel launches recorded into the graph.
 struct Stage {
-  int kind;  // 0 string phases, 1 sweep, 2 hf init, 3 dc gradient
+  int kind;  // 0 string phases, 1 sweep, 2 hf init, 3 dc gradient, 4 Slater
+             // minors, 5 Slater product + first diagonal-Coulomb gate
   int nst = 1;
   size_t jobs_off = 0;
   int njobs = 0;
@@ -301,12 +382,13 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     arena = o + bytes;
     return o;
   };
-  std::vector<size_t> o_ea(n), o_w(n), o_t(n), o_dj(n), o_cs(n);
+  std::vector<size_t> o_ea(n), o_w(n), o_t(n), o_dj(n), o_cs(n), o_sl(n);
   for (int c = 0; c < n; ++c) {
     const Circuit& C = cs[c];
     const int N = C.op->norb;
     const size_t dmax = std::max(C.sa->dim, C.sb->dim);
     o_ea[c] = take(5 * dmax * csz);
+    o_sl[c] = C.hf() && R > 0 ? take((C.sa->dim + C.sb->dim) * sizeof(double2)) : 0;
     o_w[c] = do_vjp && R > 0 ? take(C.sa->dim * C.sb->dim * csz / 2) : 0;
     o_t[c] = take((size_t)(R + 1) * N * N * 2 * sizeof(double));
     o_dj[c] = take((size_t)2 * std::max(R, 1) * N * N * sizeof(double));
@@ -326,6 +408,8 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     C.T = (double*)(base + o_t[c]);
     C.dJ = (double*)(base + o_dj[c]);
     C.colsum = (double*)(base + o_cs[c]);
+    C.sl_a = C.hf() && R > 0 ? (double2*)(base + o_sl[c]) : nullptr;
+    C.sl_b = C.hf() && R > 0 ? C.sl_a + C.sa->dim : nullptr;
   }
   // ---- parameter image: J_aa arrays, X matrices, programs, jobs
   Image img;
@@ -340,6 +424,15 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
         X[R + k].v[q] = C.op->J_ab[k * nn + q];  // reverse D_k^dag
       }
     C.xab_off = img.add(X.data(), X.size() * sizeof(Mat));
+    C.r0_off = 0;
+    if (C.hf() && R > 0) {
+      CMat R0{};
+      for (size_t q = 0; q < nn; ++q) {
+        R0.v[2 * q] = C.Rs[0][q].real();
+        R0.v[2 * q + 1] = C.Rs[0][q].imag();
+      }
+      C.r0_off = img.add(&R0, sizeof(CMat));
+    }
   }
   const size_t maxsm = (size_t)ctx->prop.sharedMemPerBlockOptin;
   const size_t half_sm = (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 - 1024;
@@ -390,17 +483,17 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     std::vector<size_t> prog_off, x_off;
   };
   std::vector<PendingSweep> pend;
-  auto sweep_stage = [&](int dir, int nst, auto&& setup) {
+  auto sweep_stage = [&](int dir, int nst, auto&& use, auto&& setup) {
     PendingSweep P;
     P.stage = stages.size();
     Stage S;
     S.kind = 1;
     S.nst = nst;
-    S.counter = ncounters++;
     int64_t items = 0;
     size_t smem = 0;
     const size_t budget = nst == 1 ? half_sm : maxsm;
     for (auto& C : cs) {
+      if (!use(C)) continue;
       PhaseDev ph;
       RevArgs rv;
       const RotProgram* rp = nullptr;
@@ -420,12 +513,15 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
       P.prog_off.push_back(img.add(plan.prog.data(), plan.prog.size()));
       P.x_off.push_back(xk >= 0 ? C.xab_off + (size_t)xk * sizeof(Mat) : (size_t)-1);
     }
+    if (P.jobs.empty()) return;
+    S.counter = ncounters++;
     S.njobs = (int)P.jobs.size();
     S.total = items;
     S.smem = smem;
     stages.push_back(S);
     pend.push_back(std::move(P));
   };
+  auto all = [](const Circuit&) { return true; };
   Mat zero{};
   const size_t zero_off = img.add(&zero, sizeof(Mat));
 
@@ -434,7 +530,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     std::vector<BVec> hv;
     int64_t tot = 0;
     for (auto& C : cs)
-      if (C.op->from_hf) {
+      if (C.hf() && R == 0) {  // with rotations the Slater start writes the state
         hv.push_back(BVec{vecs[C.idx], tot});
         tot += C.sa->dim * C.sb->dim;
       }
@@ -447,22 +543,75 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
       stages.push_back(S);
     }
   }
+  bool any_hf = false;
+  for (auto& C : cs) any_hf = any_hf || C.hf();
+  auto sweeps_k = [&](int k) {
+    // circuits from Hartree-Fock replace the first rotation (and gate) by
+    // the Slater start
+    return [k](const Circuit& C) { return k > 0 || !C.hf(); };
+  };
   for (int k = 0; k <= R && R > 0; ++k) {
     phase_stage([&](Circuit& C) {
       const int N = C.op->norb;
       std::vector<BStr> r;
+      if (k == 0 && C.hf()) {  // same-spin parts of the first gate
+        r.push_back(recipe_of(C.sa, C.ea_a, nullptr, C.jaa_off, true, 0, 1.0, N));
+        r.push_back(recipe_of(C.sb, C.ea_b, nullptr, C.jaa_off, true, 0, 1.0, N));
+        return r;
+      }
       r.push_back(recipe_of(C.sa, C.ea_a, &C.fwd[k], 0, false, 0, 0.0, N));
       r.push_back(recipe_of(C.sb, C.ea_b, &C.fwd[k], C.jaa_off, k < R, k, 1.0, N));
       if (k < R) r.push_back(recipe_of(C.sa, C.ea_o, nullptr, C.jaa_off, true, k, 1.0, N));
       return r;
     });
-    sweep_stage(0, 1, [&](Circuit& C, PhaseDev& ph, RevArgs&, const RotProgram*& rp, long& xk,
+    if (k == 0 && any_hf) {
+      std::vector<BSl> sl;
+      std::vector<BSd> sd;
+      int64_t ts = 0, tr = 0;
+      for (auto& C : cs) {
+        if (!C.hf()) continue;
+        const int N = C.op->norb;
+        // R and X pointers are image offsets + 1 until the image is placed
+        const CMat* r0 = (const CMat*)(uintptr_t)(C.r0_off + 1);
+        sl.push_back(BSl{C.sa->masks, C.sl_a, r0, ts, N, C.op->n_alpha});
+        ts += C.sa->dim;
+        sl.push_back(BSl{C.sb->masks, C.sl_b, r0, ts, N, C.op->n_beta});
+        ts += C.sb->dim;
+        BSd d{};
+        d.vec = vecs[C.idx];
+        d.va = C.sl_a;
+        d.vb = C.sl_b;
+        d.ea_a = C.ea_a;
+        d.ea_b = C.ea_b;
+        d.X = (const Mat*)(uintptr_t)(C.xab_off + 1);
+        d.ma = C.sa->masks;
+        d.mb = C.sb->masks;
+        d.db = C.sb->dim;
+        d.norb = N;
+        d.item0 = tr;
+        tr += C.sa->dim;
+        sd.push_back(d);
+      }
+      Stage S4;
+      S4.kind = 4;
+      S4.njobs = (int)sl.size();
+      S4.total = ts;
+      S4.jobs_off = img.add(sl.data(), sl.size() * sizeof(BSl));
+      stages.push_back(S4);
+      Stage S5;
+      S5.kind = 5;
+      S5.njobs = (int)sd.size();
+      S5.total = tr;
+      S5.jobs_off = img.add(sd.data(), sd.size() * sizeof(BSd));
+      stages.push_back(S5);
+    }
+    sweep_stage(0, 1, sweeps_k(k), [&](Circuit& C, PhaseDev& ph, RevArgs&, const RotProgram*& rp, long& xk,
                           bool&) {
       ph.ea_a = C.ea_a;
       rp = &C.fwd[k];
       xk = -1;
     });
-    sweep_stage(1, 1, [&](Circuit& C, PhaseDev& ph, RevArgs&, const RotProgram*& rp, long& xk,
+    sweep_stage(1, 1, sweeps_k(k), [&](Circuit& C, PhaseDev& ph, RevArgs&, const RotProgram*& rp, long& xk,
                           bool&) {
       ph.ea_b = C.ea_b;
       rp = &C.fwd[k];
@@ -484,7 +633,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
         r.push_back(recipe_of(C.sb, C.ea_b, &C.rev[m], 0, false, 0, 0.0, N));
         return r;
       });
-      sweep_stage(1, 2, [&](Circuit& C, PhaseDev& ph, RevArgs& rv, const RotProgram*& rp, long& xk,
+      sweep_stage(1, 2, all, [&](Circuit& C, PhaseDev& ph, RevArgs& rv, const RotProgram*& rp, long& xk,
                             bool& has_rev) {
         const int N = C.op->norb;
         ph.ea_b = C.ea_b;
@@ -503,7 +652,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
         }
         return r;
       });
-      sweep_stage(0, 2, [&](Circuit& C, PhaseDev& ph, RevArgs& rv, const RotProgram*& rp, long& xk,
+      sweep_stage(0, 2, all, [&](Circuit& C, PhaseDev& ph, RevArgs& rv, const RotProgram*& rp, long& xk,
                             bool& has_rev) {
         const int N = C.op->norb;
         ph.ea_a = C.ea_a;
@@ -579,13 +728,20 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
            pend[i].jobs.size() * sizeof(SweepJob));
     stages[pend[i].stage].jobs_off = job_offs[i];
   }
-  // string-phase recipes: J offsets -> device pointers
-  for (auto& S : stages)
+  // string-phase recipes and Slater jobs: image offsets -> device pointers
+  for (auto& S : stages) {
     if (S.kind == 0) {
       BStr* b = (BStr*)(img.bytes.data() + S.jobs_off);
       for (int i = 0; i < S.njobs; ++i)
         if (b[i].J) b[i].J = (const double*)(dimg + ((uintptr_t)b[i].J - 1));
+    } else if (S.kind == 4) {
+      BSl* b = (BSl*)(img.bytes.data() + S.jobs_off);
+      for (int i = 0; i < S.njobs; ++i) b[i].R = (const CMat*)(dimg + ((uintptr_t)b[i].R - 1));
+    } else if (S.kind == 5) {
+      BSd* b = (BSd*)(img.bytes.data() + S.jobs_off);
+      for (int i = 0; i < S.njobs; ++i) b[i].X = (const Mat*)(dimg + ((uintptr_t)b[i].X - 1));
     }
+  }
   memset(img.bytes.data() + counters_off, 0, std::max(ncounters, 1) * sizeof(int));
   FS_CUDA(cudaMemcpyAsync(dimg, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st));
   // accumulators start at zero
@@ -628,6 +784,15 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
       } else if (S.kind == 1) {
         launch_sweep_batch(ctx, dtype, S.nst, (const SweepJob*)jp, S.njobs, (int)S.total,
                            counters + S.counter, S.smem, cst);
+      } else if (S.kind == 4) {
+        unsigned grid = (unsigned)std::min<int64_t>((S.total + 63) / 64, 16 * sms);
+        k_slater_batch<<<grid, 64, 0, cst>>>((const BSl*)jp, S.njobs, S.total);
+      } else if (S.kind == 5) {
+        unsigned grid = (unsigned)std::min<int64_t>(S.total, 16 * sms);
+        if (dtype == FS_C64)
+          k_slater_dc_batch<float><<<grid, 256, 0, cst>>>((const BSd*)jp, S.njobs, S.total);
+        else
+          k_slater_dc_batch<double><<<grid, 256, 0, cst>>>((const BSd*)jp, S.njobs, S.total);
       } else {
         const BDc* jr = (const BDc*)jp;
         const BDc* jc = jr + S.njobs;

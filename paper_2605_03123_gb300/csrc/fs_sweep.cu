@@ -292,24 +292,6 @@ struct ProgOf<R, W, true> {
   using type = WProg<R>;
 };
 
-// exp(i x) for an FP64 angle: reduced to [-pi, pi] in FP64, then evaluated
-// in the precision of the state.
-template <typename R>
-__device__ __forceinline__ cx_t<R> expi(double x);
-template <>
-__device__ __forceinline__ cx_t<float> expi<float>(double x) {
-  double r = x - 6.283185307179586 * rint(x * 0.15915494309189535);
-  float s, c;
-  sincosf((float)r, &s, &c);
-  return mk<float>(c, s);
-}
-template <>
-__device__ __forceinline__ cx_t<double> expi<double>(double x) {
-  double r = x - 6.283185307179586 * rint(x * 0.15915494309189535);
-  double s, c;
-  sincos(r, &s, &c);
-  return mk<double>(c, s);
-}
 
 // Cross-term tables for the slab vectors o = v0 .. v0+nv-1 (other-spin
 // strings): w[kv][x] = sum_{y in I_o} X[y][x] (this = beta) or X[x][y]
@@ -1327,44 +1309,7 @@ __global__ void k_slater_minors(const uint32_t* masks, int64_t dim, int norb, in
                                 const __grid_constant__ CMat R, double2* v) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= dim) return;
-  double2 a[kMaxOrb * kMaxOrb];
-  uint32_t m = masks[e];
-  int r = 0;
-  for (int p = 0; p < norb; ++p)
-    if ((m >> p) & 1u) {
-      for (int c = 0; c < n; ++c)
-        a[r * n + c] = make_double2(R.v[2 * (p * norb + c)], R.v[2 * (p * norb + c) + 1]);
-      ++r;
-    }
-  double dr = 1, di = 0;
-  for (int k = 0; k < n; ++k) {
-    int piv = k;
-    double best = hypot(a[k * n + k].x, a[k * n + k].y);
-    for (int i = k + 1; i < n; ++i) {
-      double h = hypot(a[i * n + k].x, a[i * n + k].y);
-      if (h > best) { best = h; piv = i; }
-    }
-    if (best == 0) { dr = 0; di = 0; break; }
-    if (piv != k) {
-      for (int c = 0; c < n; ++c) { double2 t = a[k * n + c]; a[k * n + c] = a[piv * n + c]; a[piv * n + c] = t; }
-      dr = -dr; di = -di;
-    }
-    double2 pk = a[k * n + k];
-    double nr = dr * pk.x - di * pk.y;
-    di = dr * pk.y + di * pk.x;
-    dr = nr;
-    double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
-    for (int i = k + 1; i < n; ++i) {
-      double2 x = a[i * n + k];
-      double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
-      for (int c = k + 1; c < n; ++c) {
-        double2 y = a[k * n + c];
-        a[i * n + c].x -= fr * y.x - fi * y.y;
-        a[i * n + c].y -= fr * y.y + fi * y.x;
-      }
-    }
-  }
-  v[e] = make_double2(dr, di);
+  v[e] = slater_minor(masks[e], norb, n, R.v);
 }
 
 template <typename R>
