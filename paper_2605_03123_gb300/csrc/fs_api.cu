@@ -540,6 +540,25 @@ static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int
   FS_CUDA(cudaMemsetAsync(dJd, 0, 2 * R * nn * sizeof(double), st));
   double* dJaa_d = dJd;
   double* dJab_d = dJd + R * nn;
+  // Reverse alpha sweeps on a state larger than L2 run on transposed copies
+  // of psi and g (alpha strings along rows, so every slab is contiguous)
+  // when memory allows two more states; their W comes out transposed and
+  // their dJ_ab transposed, accumulated apart and transposed on the host.
+  const size_t S = (size_t)sa->dim * sb->dim * csz;
+  bool alpha_t = S > (size_t)ctx->prop.l2CacheSize;
+  if (alpha_t) {
+    size_t fr = 0, tot = 0;
+    const bool have = ctx->scratch["vjp_tpsi"].bytes >= S && ctx->scratch["vjp_tg"].bytes >= S;
+    if (!have && cudaMemGetInfo(&fr, &tot) == cudaSuccess) alpha_t = fr > 2 * S + (1ull << 30);
+  }
+  double* dJabT_d = nullptr;
+  void *tpsi = nullptr, *tg = nullptr;
+  if (alpha_t) {
+    tpsi = scratch(ctx, "vjp_tpsi", S);
+    tg = scratch(ctx, "vjp_tg", S);
+    dJabT_d = (double*)scratch(ctx, "vjp_dJabT", R * nn * sizeof(double));
+    FS_CUDA(cudaMemsetAsync(dJabT_d, 0, R * nn * sizeof(double), st));
+  }
   void* Wb = scratch(ctx, "vjp_W", sa->dim * sb->dim * (csz / 2));
   void* ea_a = scratch(ctx, "ea_a", sa->dim * csz);
   void* ea_b = scratch(ctx, "ea_b", sb->dim * csz);
@@ -573,15 +592,50 @@ static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int
       p2.has_x = 1;
       p2.X = real_mat(op->J_ab + (size_t)(m - 1) * nn, n, 1.0);
     }
-    launch_sweep(ctx, sa, sb, 0, vec, cot, 2, dtype, inv, p2, st, &r2);
-    if (m >= 1)
-      launch_dc_grad(ctx, sa, sb, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
-                     dJab_d + (size_t)(m - 1) * nn, st);
+    if (alpha_t) {
+      // the same sweep as a row sweep of the transposed states: this spin
+      // (alpha) along rows of length dim_a, the cross angles transposed
+      launch_transpose(vec, tpsi, sa->dim, sb->dim, dtype, st);
+      launch_transpose(cot, tg, sa->dim, sb->dim, dtype, st);
+      PhaseDev q2;
+      q2.ea_b = ea_a;
+      RevArgs t2;
+      t2.T = Tm;
+      if (m >= 1) {
+        t2.ea2_b = e2_a;
+        t2.ea2_a = e2_b;
+        t2.W = Wb;
+        q2.has_x = 1;
+        const double* Jab = op->J_ab + (size_t)(m - 1) * nn;
+        for (int p = 0; p < n; ++p)
+          for (int q = 0; q < n; ++q) q2.X.v[q * n + p] = Jab[p * n + q];
+      }
+      launch_sweep(ctx, sb, sa, 1, tpsi, tg, 2, dtype, inv, q2, st, &t2);
+      launch_transpose(tpsi, vec, sb->dim, sa->dim, dtype, st);
+      launch_transpose(tg, cot, sb->dim, sa->dim, dtype, st);
+      if (m >= 1)
+        launch_dc_grad(ctx, sb, sa, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
+                       dJabT_d + (size_t)(m - 1) * nn, st);
+    } else {
+      launch_sweep(ctx, sa, sb, 0, vec, cot, 2, dtype, inv, p2, st, &r2);
+      if (m >= 1)
+        launch_dc_grad(ctx, sa, sb, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
+                       dJab_d + (size_t)(m - 1) * nn, st);
+    }
   }
-  std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn);
+  std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn), dJT;
   FS_CUDA(cudaMemcpyAsync(Th.data(), Tacc, Th.size() * 8, cudaMemcpyDeviceToHost, st));
   FS_CUDA(cudaMemcpyAsync(dJh.data(), dJd, dJh.size() * 8, cudaMemcpyDeviceToHost, st));
+  if (alpha_t) {
+    dJT.resize(R * nn);
+    FS_CUDA(cudaMemcpyAsync(dJT.data(), dJabT_d, dJT.size() * 8, cudaMemcpyDeviceToHost, st));
+  }
   FS_CUDA(cudaStreamSynchronize(st));
+  if (alpha_t)
+    for (int k = 0; k < R; ++k)
+      for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+          dJh[R * nn + k * nn + p * n + q] += dJT[k * nn + q * n + p];
   if (dJ_aa) std::copy(dJh.begin(), dJh.begin() + R * nn, dJ_aa);
   if (dJ_ab) std::copy(dJh.begin() + R * nn, dJh.end(), dJ_ab);
   if (!dK) return;

@@ -360,6 +360,9 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir,
 //   dJ_ab[p][q] += sum_{ij} W_ij occ_a(i)_p occ_b(j)_q
 //   dJ_aa[p][q] += 1/2 sum_{ij} W_ij (occ_a(i)_p occ_a(i)_q + occ_b(j)_p occ_b(j)_q)
 // dJ_aa, dJ_ab: device [norb][norb] FP64 accumulators.
+// out = in^T for a [rows][cols] complex state (tiled, HBM-bound).
+void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
+                      cudaStream_t st);
 void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,
                     double* dJ_aa, double* dJ_ab, cudaStream_t st);
 

@@ -83,13 +83,25 @@ __global__ void __launch_bounds__(256)
         mma_bf16(z, a0, a1, a2, a3, __ldg(yb + t), __ldg(yb + t + 4));
       }
     }
-    // epilogue: lane holds rows (g, g+8), columns 2t, 2t+1 of the n-tile
+    // epilogue: lane holds rows (g, g+8), columns 2t, 2t+1 of the n-tile;
+    // the two columns move as one 16-byte access when the row allows it
     const int64_t jj = j0 + 8 * nt + 2 * t;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t r = h ? r1 : r0;
       if (r >= da) continue;
       const float2 fa = h ? f1 : f0;
+      float2* p = vec + r * db + jj;
+      const bool pair = jj + 1 < db && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0);
+      float2 v[2];
+      if (pair) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) v[c] = jj + c < db ? p[c] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int64_t j = jj + c;
@@ -99,9 +111,14 @@ __global__ void __launch_bounds__(256)
         const float2 fb = ea_b[j];
         const float2 fab = make_float2(fa.x * fb.x - fa.y * fb.y, fa.x * fb.y + fa.y * fb.x);
         const float2 f = make_float2(fab.x * co - fab.y * s, fab.x * s + fab.y * co);
-        float2* p = vec + r * db + j;
-        const float2 v = *p;
-        *p = make_float2(f.x * v.x - f.y * v.y, f.x * v.y + f.y * v.x);
+        v[c] = make_float2(f.x * v[c].x - f.y * v[c].y, f.x * v[c].y + f.y * v[c].x);
+      }
+      if (pair) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (jj + c < db) p[c] = v[c];
       }
     }
   }

@@ -150,4 +150,35 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
   FS_CUDA(cudaGetLastError());
 }
 
+// out[c][r] = in[r][c] for a rows x cols matrix of complex elements: 32 x 32
+// tiles through shared memory, so reads and writes are both row-contiguous.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_transpose(const T* __restrict__ in, T* __restrict__ out, int64_t rows, int64_t cols) {
+  __shared__ T tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = r0 + k, c = c0 + tx;
+    if (r < rows && c < cols) tile[k][tx] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t c = c0 + k, r = r0 + tx;
+    if (c < cols && r < rows) out[c * rows + r] = tile[tx][k];
+  }
+}
+
+void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
+                      cudaStream_t st) {
+  ProfScope ps("transpose", st);
+  FS_REQUIRE((rows + 31) / 32 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  if (dtype == FS_C64)
+    k_transpose<float2><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, rows, cols);
+  else
+    k_transpose<double2><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, rows, cols);
+  FS_CUDA(cudaGetLastError());
+}
+
 }  // namespace fs

@@ -158,6 +158,46 @@ def test_lucj_vjp_n12_central_differences(lib, lucj_small_ref):
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (trial, fd, an)
 
 
+def test_lucj_vjp_n16_central_differences(lib):
+    """N=16 (8,8), complex128, 2 layers of the metric workload from a random
+    state: the state (2.65 GB) exceeds L2, so the reverse alpha sweeps run on
+    transposed copies; central differences (step 1e-5) along random
+    directions against the VJP, in all parameters, with the loss reduced on
+    the device in row blocks."""
+    w = inputs.lucj_layers(16, (8, 8), 2, 0.5, 0.3, 2000 + 7, with_cot=False)
+    norb, nelec = 16, (8, 8)
+    K, Jaa, Jab = w["K"], w["J_aa"], w["J_ab"]
+    v0 = inputs.device_state(norb, nelec, 41, torch.complex128)
+    cot = inputs.device_state(norb, nelec, 42, torch.complex128)
+
+    def loss(K_, Ja_, Jb_):
+        x = v0.clone()
+        lib.lucj_forward_(x, K_, Ja_, Jb_, norb, nelec)
+        return _vdot_rows(cot, x).real
+
+    x = v0.clone()
+    lib.lucj_forward_(x, K, Jaa, Jab, norb, nelec)
+    cg = cot.clone()
+    dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec)
+    assert float((x - v0).abs().max().item()) < 1e-10
+    g = inputs.rng(31338)
+    h = 1e-5
+    for trial in range(2):
+        eK = np.array([inputs.random_antihermitian(norb, 1.0, g) for _ in range(len(K))])
+        eA = np.array([inputs.random_symmetric(norb, 1.0, g) for _ in range(len(K))])
+        eB = np.array([g.normal(0, 1, (norb, norb)) for _ in range(len(K))])
+        fd = (loss(K + h * eK, Jaa + h * eA, Jab + h * eB)
+              - loss(K - h * eK, Jaa - h * eA, Jab - h * eB)) / (2 * h)
+        an = (np.sum(dK.real * eK.real + dK.imag * eK.imag) + np.sum(dJa * eA)
+              + np.sum(dJb * eB))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (trial, fd, an)
+    # the mixed-coupling gradient alone (the part that comes out transposed)
+    eB = np.array([g.normal(0, 1, (norb, norb)) for _ in range(len(K))])
+    fd = (loss(K, Jaa, Jab + h * eB) - loss(K, Jaa, Jab - h * eB)) / (2 * h)
+    an = np.sum(dJb * eB)
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (fd, an)
+
+
 @pytest.mark.parametrize("dt", ["c64", "c128"])
 def test_lucj_vjp_full_size_properties(lib, dt):
     """N=16 (8,8), 2 layers of the metric workload: the reverse sweeps recover
