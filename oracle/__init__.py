@@ -9,11 +9,13 @@ Plain, slow, obviously-correct complex128 NumPy/SciPy code written from the
 paper: string addresses (§3.1), number-operator-sum and diagonal-Coulomb
 evolution (§3.2.1, §3.2.2), orbital rotations by minor determinants (§2.3)
 and by Givens rotations (§3.2.3), the LUCJ ansatz (§4.3, §4.5.1) and its
-gradient.  Each function is pinned by tests that do not reuse it: a dense
+gradient, the remaining gates of Table 1, and Trotter-Suzuki time evolution
+of double-factorized and diagonal-Coulomb Hamiltonians.  Each function is pinned by tests that do not reuse it: a dense
 Jordan-Wigner construction with matrix exponentials (`bruteforce`), the
 Slater-determinant closed form (§2.4), the group-homomorphism identities of
 §2.3, the gate equivalences listed after Table 1, the state sizes printed in
-§1, §5.2 and §6.1, and finite differences for the gradient.
+§1, §5.2 and §6.1, finite differences for the gradient, and the convergence
+order of the product formulas against exact evolution.
 """
 
 from .strings import strings, address_map, occupations, excite
@@ -26,3 +28,7 @@ from .gates import (dims, hartree_fock, apply_num_op_sum_evolution,
                     slater_from_hf)
 from .lucj import (lucj_forward, lucj_vjp, transition_one_body,
                    expm_frechet_adjoint)
+from .trotter import (apply_num_interaction, apply_num_num_interaction,
+                      apply_givens_rotation, apply_tunneling_interaction,
+                      apply_quad_ham_evolution, product_formula,
+                      simulate_trotter_double_factorized, simulate_trotter_diag_coulomb)
