@@ -338,6 +338,7 @@ def run_gpu(args):
         if args.extras:
             out["dc_phase"] = run_dc_phase(args, ctx)
             out["small_rotation"] = run_small_rotation(args, ctx)
+            out["trotter"] = run_trotter(args, ctx)
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -522,6 +523,39 @@ def run_dc_phase(args, ctx):
         out[name] = {"ms": ms, "algorithmic_bytes": 2 * S, "achieved_gbs": gbs,
                      "frac": gbs / peak}
         del v
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_trotter(args, ctx):
+    """Trotter simulation of a double-factorized Hamiltonian at N=16 (8,8):
+    three order-0 steps of a Hamiltonian with a one-body term and three
+    two-body terms (the paper's Trotter benchmark shape), from a random
+    state; complex64 and complex128."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    g = inputs.rng(2300)
+    A = g.normal(0, 0.5, (16, 16)) + 1j * g.normal(0, 0.5, (16, 16))
+    h = (A + A.conj().T) / 2
+    Js = np.array([inputs.random_symmetric(16, 0.5, g) for _ in range(3)])
+    Us = np.array([inputs.haar_unitary(16, g) for _ in range(3)])
+    v0 = inputs.device_state(16, (8, 8), 9, torch.complex128)
+    out = {"workload": "trotter_double_factorized_norb16_nelec8_8_3terms_3steps_order0",
+           "unit": "ms per evolution (3 Trotter steps)"}
+    for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        x = v0.to(dt)
+        f = lambda: fsgpu.simulate_trotter_double_factorized_(x, h, Js, Us, 1.0, 16, (8, 8),
+                                                              n_steps=3, order=0, ctx=ctx)
+        f()
+        ctx.profile_start()
+        ms = _timed(f)
+        prof = ctx.profile_stop()
+        out[name] = {"ms": ms, "trotter_steps_per_s": 3 / (ms / 1e3),
+                     "kernels": {k: {"records": v[0], "ms": round(v[1], 3)}
+                                 for k, v in prof.items()}}
+        del x
+    out["c64_speedup"] = out["c128"]["ms"] / out["c64"]["ms"]
+    del v0
     torch.cuda.empty_cache()
     return out
 

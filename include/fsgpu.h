@@ -200,6 +200,69 @@ int fs_lucj_vjp(fs_ctx *ctx, const fs_lucj *op, void *vec, void *cot,
                 int dtype, double *dK, double *dJ_aa, double *dJ_ab,
                 void *stream);
 
+/* ---- Remaining gates of Table 1 (each a special case of the gates above,
+ * as listed after Table 1).  `spins` is a mask: 1 = alpha, 2 = beta,
+ * 3 = both (the two spin parts commute).  All act in place on `vec` on the
+ * stream, like fs_apply_orbital_rotation; orbital indices are 0-based.
+ *
+ * Number interaction exp(i theta n_{p sigma}). */
+int fs_apply_num_interaction(fs_ctx *ctx, void *vec, int dtype, double theta, int p, int spins,
+                             int norb, int n_alpha, int n_beta, void *stream);
+/* Number-number interaction exp(i theta n_{p sigma} n_{q tau}); sigma, tau
+ * are 0 (alpha) or 1 (beta); p == q with sigma == tau is n_p. */
+int fs_apply_num_num_interaction(fs_ctx *ctx, void *vec, int dtype, double theta, int p,
+                                 int sigma, int q, int tau, int norb, int n_alpha, int n_beta,
+                                 void *stream);
+/* Givens rotation exp(theta (a^dag_p a_q - a^dag_q a_p)) on the spins of
+ * the mask (p != q): the orbital rotation by expm(theta (E_pq - E_qp)). */
+int fs_apply_givens_rotation(fs_ctx *ctx, void *vec, int dtype, double theta, int p, int q,
+                             int spins, int norb, int n_alpha, int n_beta, void *stream);
+/* Tunneling interaction exp(i theta (a^dag_p a_q + a^dag_q a_p)) on the
+ * spins of the mask (p != q): the orbital rotation by
+ * expm(i theta (E_pq + E_qp)). */
+int fs_apply_tunneling_interaction(fs_ctx *ctx, void *vec, int dtype, double theta, int p,
+                                   int q, int spins, int norb, int n_alpha, int n_beta,
+                                   void *stream);
+/* Quadratic Hamiltonian evolution exp(-i t sum_{pq sigma} M^sigma_pq
+ * a^dag_{p sigma} a_{q sigma}): the orbital rotation by expm(-i M t) per
+ * spin.  M_a, M_b: host N x N complex Hermitian (interleaved), M_b NULL
+ * means M_a; FS_ERR_ARG if not Hermitian to 1e-10. */
+int fs_apply_quad_ham_evolution(fs_ctx *ctx, void *vec, int dtype, const double *M_a,
+                                const double *M_b, double t, int norb, int n_alpha, int n_beta,
+                                void *stream);
+
+/* ---- Trotter-Suzuki time evolution (Hamiltonian time evolution section).
+ * exp(-i H time) vec ~ S_order(time / n_steps)^n_steps with
+ *   S_0(t) = exp(-i H_L t) .. exp(-i H_1 t),
+ *   S_1(t) = exp(-i H_1 t/2) .. exp(-i H_L t/2) exp(-i H_L t/2) .. exp(-i H_1 t/2),
+ *   S_k(t) = S_{k-1}(u_k t)^2 S_{k-1}((1 - 4 u_k) t) S_{k-1}(u_k t)^2,
+ *   u_k = 1 / (4 - 4^{1/(2k-1)}),  order in 0 .. 6, n_steps >= 1.
+ * H_1 is the one-body term sum_{pq sigma} h_pq a^dag a (exponential: the
+ * orbital rotation by expm(-i h t)); the two-body terms follow in order.
+ * Neighbouring factors of the same term are joined, neighbouring rotations
+ * multiplied on the host, and every diagonal-Coulomb evolution runs fused
+ * into a rotation's beta sweep.  In place on `vec`, on the stream.
+ *
+ * Double-factorized Hamiltonian (eq. for the double factorized form):
+ * H = sum h_pq a^dag a + 1/2 sum_t sum_{pq sigma tau} J^(t)_pq n^(t)_{p sigma}
+ * n^(t)_{q tau}, n^(t)_p the number operator rotated by U^(t); term t's
+ * exponential is U(U^(t)) DC(J^(t), t) U(U^(t))^dag.  one_body: N x N
+ * complex Hermitian; diag_coulomb_mats: n_terms x N x N real symmetric;
+ * orbital_rotations: n_terms x N x N complex unitary (interleaved). */
+int fs_simulate_trotter_double_factorized(fs_ctx *ctx, void *vec, int dtype,
+                                          const double *one_body, int n_terms,
+                                          const double *diag_coulomb_mats,
+                                          const double *orbital_rotations, double time,
+                                          int n_steps, int order, int norb, int n_alpha,
+                                          int n_beta, void *stream);
+/* Diagonal-Coulomb Hamiltonian H = sum h_pq a^dag a + 1/2 sum_{pq sigma tau}
+ * J^{sigma tau}_pq n_{p sigma} n_{q tau} (J^{beta alpha} = J_ab^T, J_bb NULL
+ * means J_aa): H_1 the one-body term, H_2 the diagonal-Coulomb term. */
+int fs_simulate_trotter_diag_coulomb(fs_ctx *ctx, void *vec, int dtype, const double *one_body,
+                                     const double *J_aa, const double *J_ab,
+                                     const double *J_bb, double time, int n_steps, int order,
+                                     int norb, int n_alpha, int n_beta, void *stream);
+
 /* Batched LUCJ (the ansatz of fs_lucj_forward, many independent circuits,
  * uneven sectors): ops[c], vecs[c], cots[c] describe circuit c exactly as
  * for fs_lucj_forward (and, when do_vjp, fs_lucj_vjp, which then follows

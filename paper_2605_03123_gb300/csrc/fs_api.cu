@@ -105,6 +105,7 @@ static StrPhase phase_of(const RotProgram* rp, const double* J, double t, const 
 struct Fused {
   const double* J_aa = nullptr;  // host, N x N
   const double* J_ab = nullptr;  // host, N x N
+  const double* J_bb = nullptr;  // host, N x N; null means J_aa
   double t = 0;
 };
 
@@ -125,7 +126,8 @@ static void rotate(Ctx* ctx, Space* sa, Space* sb, void* v0, void* v1, int nst, 
   launch_sweep(ctx, sa, sb, 0, v0, v1, nst, dtype, pa, ph, st);
   PhaseDev phb;
   if (dc) {
-    launch_string_phase(sb, ea_b, dtype, phase_of(&pb, dc->J_aa, dc->t, nullptr, n), st);
+    launch_string_phase(sb, ea_b, dtype,
+                        phase_of(&pb, dc->J_bb ? dc->J_bb : dc->J_aa, dc->t, nullptr, n), st);
     launch_string_phase(sa, ea_o, dtype, phase_of(nullptr, dc->J_aa, dc->t, nullptr, n), st);
     phb.ea_a = ea_o;
     phb.has_x = 1;
@@ -260,6 +262,125 @@ static std::vector<std::vector<zd>> lucj_rotations(const fs_lucj* op,
   Rs[R] = Us[R - 1];
   if (Us_out) *Us_out = Us;
   return Rs;
+}
+
+// ------------------------------------------------------------ gate lists
+// A circuit of orbital rotations and diagonal-Coulomb evolutions, applied
+// with neighbouring rotations multiplied on the host (U(A) U(B) = U(AB),
+// §2.3) and every diagonal-Coulomb evolution fused into the beta sweep of
+// the rotation before it; one that follows no rotation runs as a phase pass.
+struct GateOp {
+  int kind = 0;             // 0 orbital rotation, 1 diagonal-Coulomb evolution
+  std::vector<zd> Ua, Ub;   // kind 0
+  const double *J_aa = nullptr, *J_ab = nullptr, *J_bb = nullptr;  // kind 1
+  double t = 0;             // kind 1
+};
+
+static void run_gates(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
+                      const std::vector<GateOp>& ops, cudaStream_t st) {
+  const int n = sa->norb;
+  const size_t nn = (size_t)n * n;
+  std::vector<zd> I(nn, zd(0)), Pa, Pb, tmp(nn);
+  for (int p = 0; p < n; ++p) I[p * n + p] = 1;
+  Pa = I;
+  Pb = I;
+  bool pending = false;
+  auto flush = [&](const GateOp* dc) {
+    if (pending) {
+      RotProgram pa = decompose_adjacent(n, Pa.data());
+      RotProgram pb = decompose_adjacent(n, Pb.data());
+      Fused f;
+      if (dc) {
+        f.J_aa = dc->J_aa;
+        f.J_ab = dc->J_ab;
+        f.J_bb = dc->J_bb;
+        f.t = dc->t;
+      }
+      rotate(ctx, sa, sb, vec, nullptr, 1, dtype, pa, pb, dc ? &f : nullptr, st);
+    } else if (dc) {
+      phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, dc->J_aa, dc->t, nullptr, n),
+                 phase_of(nullptr, dc->J_bb ? dc->J_bb : dc->J_aa, dc->t, nullptr, n), dc->J_ab,
+                 -dc->t, st);
+    }
+    Pa = I;
+    Pb = I;
+    pending = false;
+  };
+  for (const GateOp& op : ops) {
+    if (op.kind == 0) {
+      mat_mul(n, op.Ua.data(), Pa.data(), tmp.data());
+      Pa = tmp;
+      mat_mul(n, op.Ub.data(), Pb.data(), tmp.data());
+      Pb = tmp;
+      pending = true;
+    } else {
+      flush(&op);
+    }
+  }
+  flush(nullptr);
+}
+
+// S_order(t) of the Trotter-Suzuki product formulas (Hamiltonian time
+// evolution section) as (term, time) pairs, first factor first:
+// S_0 = H_1 .. H_L, S_1 = H_1/2 .. H_L/2 H_L/2 .. H_1/2,
+// S_k = S_{k-1}(u t)^2 S_{k-1}((1 - 4u) t) S_{k-1}(u t)^2, u = 1/(4 - 4^{1/(2k-1)}).
+static void product_formula(int L, double t, int order,
+                            std::vector<std::pair<int, double>>& out) {
+  if (order == 0) {
+    for (int j = 0; j < L; ++j) out.emplace_back(j, t);
+  } else if (order == 1) {
+    for (int j = 0; j < L; ++j) out.emplace_back(j, t / 2);
+    for (int j = L - 1; j >= 0; --j) out.emplace_back(j, t / 2);
+  } else {
+    const double u = 1.0 / (4.0 - std::pow(4.0, 1.0 / (2 * order - 1)));
+    for (int r = 0; r < 2; ++r) product_formula(L, u * t, order - 1, out);
+    product_formula(L, (1 - 4 * u) * t, order - 1, out);
+    for (int r = 0; r < 2; ++r) product_formula(L, u * t, order - 1, out);
+  }
+}
+
+// The (term, time) sequence of n_steps steps of S_order(time / n_steps),
+// with neighbouring factors of the same term joined (exp(-i H_j a)
+// exp(-i H_j b) = exp(-i H_j (a + b)), exact).
+static std::vector<std::pair<int, double>> trotter_sequence(int L, double time, int n_steps,
+                                                            int order) {
+  std::vector<std::pair<int, double>> one, all;
+  product_formula(L, time / n_steps, order, one);
+  for (int r = 0; r < n_steps; ++r)
+    for (const auto& f : one) {
+      if (!all.empty() && all.back().first == f.first)
+        all.back().second += f.second;
+      else
+        all.push_back(f);
+    }
+  return all;
+}
+
+// exp(-i t M) for an N x N Hermitian M (host, FP64).
+static std::vector<zd> expm_minus_i(int n, const std::vector<zd>& M, double t) {
+  std::vector<zd> K(M.size()), U(M.size());
+  for (size_t q = 0; q < M.size(); ++q) K[q] = zd(0, -t) * M[q];
+  expm(n, K.data(), U.data());
+  return U;
+}
+
+static std::vector<zd> adjoint_of(int n, const std::vector<zd>& U) {
+  std::vector<zd> A(U.size());
+  mat_adjoint(n, U.data(), A.data());
+  return A;
+}
+
+static void check_hermitian(const std::vector<zd>& M, int n, const char* what) {
+  double err = 0, scale = 1;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      err = std::max(err, std::abs(M[p * n + q] - std::conj(M[q * n + p])));
+      scale = std::max(scale, std::abs(M[p * n + q]));
+    }
+  if (err > 1e-10 * scale) {
+    set_error(std::string(what) + " is not Hermitian");
+    throw Fail{FS_ERR_ARG};
+  }
 }
 
 }  // namespace fs
@@ -506,6 +627,252 @@ int fs_lucj_forward(fs_ctx* ctx, const fs_lucj* op, void* vec, int dtype, void* 
         rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, nullptr, st);
       }
     }
+  });
+}
+
+// ------------------------------------------------- remaining Table 1 gates
+static void spin_mask_check(int spins) {
+  FS_REQUIRE(spins >= 1 && spins <= 3, FS_ERR_ARG, "spin mask must be 1 (alpha), 2 (beta) or 3");
+}
+
+static void orb_check(int p, int norb) {
+  FS_REQUIRE(p >= 0 && p < norb, FS_ERR_ARG, "orbital index out of range");
+}
+
+int fs_apply_num_interaction(fs_ctx* ctx, void* vec, int dtype, double theta, int p, int spins,
+                             int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    spin_mask_check(spins);
+    orb_check(p, norb);
+    FS_REQUIRE(std::isfinite(theta), FS_ERR_ARG, "theta must be finite");
+    // exp(i theta n_p) = number-operator-sum evolution with lambda = e_p, t = -theta
+    std::vector<double> la(norb, 0.0), lb(norb, 0.0);
+    if (spins & 1) la[p] = 1;
+    if (spins & 2) lb[p] = 1;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, nullptr, -theta, la.data(), norb),
+               phase_of(nullptr, nullptr, -theta, lb.data(), norb), nullptr, 0, st);
+  });
+}
+
+int fs_apply_num_num_interaction(fs_ctx* ctx, void* vec, int dtype, double theta, int p,
+                                 int sigma, int q, int tau, int norb, int na, int nb,
+                                 void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    orb_check(p, norb);
+    orb_check(q, norb);
+    FS_REQUIRE((sigma == 0 || sigma == 1) && (tau == 0 || tau == 1), FS_ERR_ARG,
+               "spins must be 0 (alpha) or 1 (beta)");
+    FS_REQUIRE(std::isfinite(theta), FS_ERR_ARG, "theta must be finite");
+    // diagonal-Coulomb evolution at t = -theta whose exponent is n_{p sigma} n_{q tau}
+    const size_t nn = (size_t)norb * norb;
+    std::vector<double> Jaa(nn, 0.0), Jab(nn, 0.0), Jbb(nn, 0.0);
+    if (sigma == tau) {
+      std::vector<double>& J = sigma == 0 ? Jaa : Jbb;
+      if (p == q) {
+        J[p * norb + p] = 2;  // -1/2 t J_pp n_p n_p with n_p^2 = n_p
+      } else {
+        J[p * norb + q] = 1;
+        J[q * norb + p] = 1;
+      }
+    } else if (sigma == 0) {
+      Jab[p * norb + q] = 1;  // the mixed term counts J_ab twice
+    } else {
+      Jab[q * norb + p] = 1;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    phase_pass(ctx, sa, sb, vec, dtype, phase_of(nullptr, Jaa.data(), -theta, nullptr, norb),
+               phase_of(nullptr, Jbb.data(), -theta, nullptr, norb),
+               sigma == tau ? nullptr : Jab.data(), theta, st);
+  });
+}
+
+// Orbital rotation by expm(K) on the spins of the mask (identity on the
+// others), K the one-body generator of a Table 1 gate.
+static void generator_rotation(fs_ctx* ctx, void* vec, int dtype, const std::vector<zd>& K,
+                               int spins, int norb, int na, int nb, void* stream) {
+  const size_t nn = (size_t)norb * norb;
+  std::vector<zd> U(nn), I(nn, zd(0));
+  for (int p = 0; p < norb; ++p) I[p * norb + p] = 1;
+  expm(norb, K.data(), U.data());
+  const std::vector<zd>& Ua = (spins & 1) ? U : I;
+  const std::vector<zd>& Ub = (spins & 2) ? U : I;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  current_ctx() = ctx;
+  FS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Space* sa = get_space(ctx, norb, na, st);
+  Space* sb = get_space(ctx, norb, nb, st);
+  RotProgram pa = decompose_adjacent(norb, Ua.data());
+  RotProgram pb = decompose_adjacent(norb, Ub.data());
+  rotate_any(ctx, sa, sb, vec, dtype, Ua, Ub, pa, pb, st);
+}
+
+int fs_apply_givens_rotation(fs_ctx* ctx, void* vec, int dtype, double theta, int p, int q,
+                             int spins, int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    spin_mask_check(spins);
+    orb_check(p, norb);
+    orb_check(q, norb);
+    FS_REQUIRE(p != q, FS_ERR_ARG, "a Givens rotation needs two distinct orbitals");
+    FS_REQUIRE(std::isfinite(theta), FS_ERR_ARG, "theta must be finite");
+    // theta (a^dag_p a_q - a^dag_q a_p) = sum K_rs a^dag_r a_s
+    std::vector<zd> K((size_t)norb * norb, zd(0));
+    K[p * norb + q] = theta;
+    K[q * norb + p] = -theta;
+    generator_rotation(ctx, vec, dtype, K, spins, norb, na, nb, stream);
+  });
+}
+
+int fs_apply_tunneling_interaction(fs_ctx* ctx, void* vec, int dtype, double theta, int p,
+                                   int q, int spins, int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    spin_mask_check(spins);
+    orb_check(p, norb);
+    orb_check(q, norb);
+    FS_REQUIRE(p != q, FS_ERR_ARG, "a tunneling interaction needs two distinct orbitals");
+    FS_REQUIRE(std::isfinite(theta), FS_ERR_ARG, "theta must be finite");
+    // i theta (a^dag_p a_q + a^dag_q a_p) = sum K_rs a^dag_r a_s
+    std::vector<zd> K((size_t)norb * norb, zd(0));
+    K[p * norb + q] = zd(0, theta);
+    K[q * norb + p] = zd(0, theta);
+    generator_rotation(ctx, vec, dtype, K, spins, norb, na, nb, stream);
+  });
+}
+
+int fs_apply_quad_ham_evolution(fs_ctx* ctx, void* vec, int dtype, const double* M_a,
+                                const double* M_b, double t, int norb, int na, int nb,
+                                void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    FS_REQUIRE(M_a != nullptr, FS_ERR_ARG, "null M_a");
+    FS_REQUIRE(std::isfinite(t), FS_ERR_ARG, "t must be finite");
+    std::vector<zd> Ma = load_cmat(M_a, norb);
+    std::vector<zd> Mb = M_b ? load_cmat(M_b, norb) : Ma;
+    check_hermitian(Ma, norb, "M_a");
+    if (M_b) check_hermitian(Mb, norb, "M_b");
+    // exp(-i t sum M_pq a^dag_p a_q) = U(expm(-i M t)) per spin
+    std::vector<zd> Ua = expm_minus_i(norb, Ma, t);
+    std::vector<zd> Ub = M_b ? expm_minus_i(norb, Mb, t) : Ua;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    RotProgram pa = decompose_adjacent(norb, Ua.data());
+    RotProgram pb = M_b ? decompose_adjacent(norb, Ub.data()) : pa;
+    rotate_any(ctx, sa, sb, vec, dtype, Ua, Ub, pa, pb, st);
+  });
+}
+
+// ------------------------------------------------------------ Trotter
+static void trotter_checks(double time, int n_steps, int order) {
+  FS_REQUIRE(std::isfinite(time), FS_ERR_ARG, "time must be finite");
+  FS_REQUIRE(n_steps >= 1, FS_ERR_ARG, "n_steps must be >= 1");
+  FS_REQUIRE(order >= 0 && order <= 6, FS_ERR_ARG, "order must be in 0 .. 6");
+}
+
+int fs_simulate_trotter_double_factorized(fs_ctx* ctx, void* vec, int dtype,
+                                          const double* one_body, int n_terms,
+                                          const double* diag_coulomb_mats,
+                                          const double* orbital_rotations, double time,
+                                          int n_steps, int order, int norb, int na, int nb,
+                                          void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    trotter_checks(time, n_steps, order);
+    FS_REQUIRE(one_body != nullptr, FS_ERR_ARG, "null one-body tensor");
+    FS_REQUIRE(n_terms >= 0 && (n_terms == 0 || (diag_coulomb_mats && orbital_rotations)),
+               FS_ERR_ARG, "bad two-body terms");
+    const size_t nn = (size_t)norb * norb;
+    std::vector<zd> h = load_cmat(one_body, norb);
+    check_hermitian(h, norb, "one-body tensor");
+    std::vector<std::vector<zd>> U(n_terms), Ud(n_terms);
+    for (int k = 0; k < n_terms; ++k) {
+      U[k] = load_cmat(orbital_rotations + 2 * nn * k, norb);
+      check_unitary(U[k], norb, "orbital rotation");
+      Ud[k] = adjoint_of(norb, U[k]);
+    }
+    std::vector<GateOp> ops;
+    for (const auto& f : trotter_sequence(1 + n_terms, time, n_steps, order)) {
+      if (f.first == 0) {
+        GateOp g;
+        g.Ua = g.Ub = expm_minus_i(norb, h, f.second);
+        ops.push_back(std::move(g));
+      } else {
+        // U(U_t) DC(J_t on every spin pair, time) U(U_t)^dag
+        const int k = f.first - 1;
+        const double* J = diag_coulomb_mats + nn * k;
+        GateOp r0;
+        r0.Ua = r0.Ub = Ud[k];
+        ops.push_back(std::move(r0));
+        GateOp d;
+        d.kind = 1;
+        d.J_aa = d.J_ab = d.J_bb = J;
+        d.t = f.second;
+        ops.push_back(d);
+        GateOp r1;
+        r1.Ua = r1.Ub = U[k];
+        ops.push_back(std::move(r1));
+      }
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    run_gates(ctx, sa, sb, vec, dtype, ops, st);
+  });
+}
+
+int fs_simulate_trotter_diag_coulomb(fs_ctx* ctx, void* vec, int dtype, const double* one_body,
+                                     const double* J_aa, const double* J_ab,
+                                     const double* J_bb, double time, int n_steps, int order,
+                                     int norb, int na, int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, vec, dtype, norb, na, nb);
+    trotter_checks(time, n_steps, order);
+    FS_REQUIRE(one_body != nullptr && J_aa != nullptr && J_ab != nullptr, FS_ERR_ARG,
+               "null Hamiltonian array");
+    std::vector<zd> h = load_cmat(one_body, norb);
+    check_hermitian(h, norb, "one-body tensor");
+    std::vector<GateOp> ops;
+    for (const auto& f : trotter_sequence(2, time, n_steps, order)) {
+      GateOp g;
+      if (f.first == 0) {
+        g.Ua = g.Ub = expm_minus_i(norb, h, f.second);
+      } else {
+        g.kind = 1;
+        g.J_aa = J_aa;
+        g.J_ab = J_ab;
+        g.J_bb = J_bb ? J_bb : J_aa;
+        g.t = f.second;
+      }
+      ops.push_back(std::move(g));
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    run_gates(ctx, sa, sb, vec, dtype, ops, st);
   });
 }
 

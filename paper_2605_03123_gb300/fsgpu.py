@@ -58,6 +58,15 @@ SIGNATURES = {
     "fs_apply_diag_coulomb_evolution_noalloc": [_P, _I, _P, _P, _P, _D, _I, _I, _I, _P],
     "fs_lucj_forward": [_P, ctypes.POINTER(LUCJ), _P, _I, _P],
     "fs_lucj_vjp": [_P, ctypes.POINTER(LUCJ), _P, _P, _I, _P, _P, _P, _P],
+    "fs_apply_num_interaction": [_P, _P, _I, _D, _I, _I, _I, _I, _I, _P],
+    "fs_apply_num_num_interaction": [_P, _P, _I, _D, _I, _I, _I, _I, _I, _I, _I, _P],
+    "fs_apply_givens_rotation": [_P, _P, _I, _D, _I, _I, _I, _I, _I, _I, _P],
+    "fs_apply_tunneling_interaction": [_P, _P, _I, _D, _I, _I, _I, _I, _I, _I, _P],
+    "fs_apply_quad_ham_evolution": [_P, _P, _I, _P, _P, _D, _I, _I, _I, _P],
+    "fs_simulate_trotter_double_factorized": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _I, _I, _I,
+                                              _I, _P],
+    "fs_simulate_trotter_diag_coulomb": [_P, _P, _I, _P, _P, _P, _P, _D, _I, _I, _I, _I, _I,
+                                         _P],
     "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                       _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
 }
@@ -330,3 +339,84 @@ def lucj_batch_(vecs, cots, circuits, do_vjp=True, ctx=None):
     _check("fs_lucj_batch", load_library().fs_lucj_batch(
         ctx.handle, n, ops, pv, pc, dt, int(bool(do_vjp)), pK, pA, pB, _stream_ptr()))
     return grads if do_vjp else [None] * n
+
+
+# ------------------------------------------------- remaining Table 1 gates
+_SPINS = {"alpha": 1, "beta": 2, "both": 3, 1: 1, 2: 2, 3: 3}
+
+
+def _spins(spin):
+    if spin not in _SPINS:
+        raise ValueError("spin must be 'alpha', 'beta' or 'both'")
+    return _SPINS[spin]
+
+
+def _spin_index(s):
+    return {"alpha": 0, "beta": 1, 0: 0, 1: 1}[s]
+
+
+def _state_call(name, vec, norb, nelec, ctx, *args):
+    _check_state(vec, norb, nelec)
+    ctx = ctx or context(vec.device.index)
+    _check(name, getattr(load_library(), name)(
+        ctx.handle, _P(vec.data_ptr()), _dtype_code(vec), *args, norb, nelec[0], nelec[1],
+        _stream_ptr()))
+    return vec
+
+
+def apply_num_interaction_(vec, theta, p, norb, nelec, spin="both", ctx=None):
+    """exp(i theta n_{p sigma}) in place (Table 1)."""
+    return _state_call("fs_apply_num_interaction", vec, norb, nelec, ctx, float(theta), int(p),
+                       _spins(spin))
+
+
+def apply_num_num_interaction_(vec, theta, p, q, norb, nelec, spins=("alpha", "alpha"),
+                               ctx=None):
+    """exp(i theta n_{p sigma} n_{q tau}) in place (Table 1); spins = (sigma, tau)."""
+    return _state_call("fs_apply_num_num_interaction", vec, norb, nelec, ctx, float(theta),
+                       int(p), _spin_index(spins[0]), int(q), _spin_index(spins[1]))
+
+
+def apply_givens_rotation_(vec, theta, p, q, norb, nelec, spin="both", ctx=None):
+    """exp(theta (a^dag_p a_q - a^dag_q a_p)) in place (Table 1)."""
+    return _state_call("fs_apply_givens_rotation", vec, norb, nelec, ctx, float(theta), int(p),
+                       int(q), _spins(spin))
+
+
+def apply_tunneling_interaction_(vec, theta, p, q, norb, nelec, spin="both", ctx=None):
+    """exp(i theta (a^dag_p a_q + a^dag_q a_p)) in place (Table 1)."""
+    return _state_call("fs_apply_tunneling_interaction", vec, norb, nelec, ctx, float(theta),
+                       int(p), int(q), _spins(spin))
+
+
+def apply_quad_ham_evolution_(vec, M, t, norb, nelec, M_b=None, ctx=None):
+    """exp(-i t sum M_pq a^dag_p a_q) in place, per spin (Table 1)."""
+    Ma = _f64(M, (norb, norb), True)
+    Mb = None if M_b is None else _f64(M_b, (norb, norb), True)
+    return _state_call("fs_apply_quad_ham_evolution", vec, norb, nelec, ctx, _ptr(Ma), _ptr(Mb),
+                       float(t))
+
+
+# ------------------------------------------------------------ Trotter
+def simulate_trotter_double_factorized_(vec, one_body, diag_coulomb_mats, orbital_rotations,
+                                        time, norb, nelec, n_steps=1, order=0, ctx=None):
+    """Trotter-Suzuki evolution by a double-factorized Hamiltonian, in place."""
+    h = _f64(one_body, (norb, norb), True)
+    J = _f64(diag_coulomb_mats)
+    U = _f64(orbital_rotations, None, True)
+    n_terms = J.shape[0] if J.ndim == 3 else 0
+    if n_terms and (J.shape != (n_terms, norb, norb) or U.shape != (n_terms, norb, norb)):
+        raise ValueError("diag_coulomb_mats and orbital_rotations must be (n_terms, norb, norb)")
+    return _state_call("fs_simulate_trotter_double_factorized", vec, norb, nelec, ctx, _ptr(h),
+                       n_terms, _ptr(J) if n_terms else None, _ptr(U) if n_terms else None,
+                       float(time), int(n_steps), int(order))
+
+
+def simulate_trotter_diag_coulomb_(vec, one_body, J_aa, J_ab, time, norb, nelec, n_steps=1,
+                                   order=0, J_bb=None, ctx=None):
+    """Trotter-Suzuki evolution by a diagonal-Coulomb Hamiltonian, in place."""
+    h = _f64(one_body, (norb, norb), True)
+    Ja, Jb = _f64(J_aa, (norb, norb)), _f64(J_ab, (norb, norb))
+    Jbb = None if J_bb is None else _f64(J_bb, (norb, norb))
+    return _state_call("fs_simulate_trotter_diag_coulomb", vec, norb, nelec, ctx, _ptr(h),
+                       _ptr(Ja), _ptr(Jb), _ptr(Jbb), float(time), int(n_steps), int(order))
