@@ -339,6 +339,7 @@ def run_gpu(args):
             out["dc_phase"] = run_dc_phase(args, ctx)
             out["small_rotation"] = run_small_rotation(args, ctx)
             out["trotter"] = run_trotter(args, ctx)
+            out["operator_action"] = run_operator_action(args, ctx)
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -558,6 +559,37 @@ def run_trotter(args, ctx):
     del v0
     torch.cuda.empty_cache()
     return out
+
+
+def run_operator_action(args, ctx):
+    """H psi for a molecular Hamiltonian with random real symmetric tensors
+    (8-fold symmetric h_pqrs) at N=12 (6,6) and N=16 (4,4): milliseconds per
+    application and the GEMM rate (2 * N^2 * 3N^2 * 2 * dim flops)."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    res = {"unit": "ms per application"}
+    for N, ne in ((12, (6, 6)), (16, (4, 4))):
+        g = inputs.rng(2400 + N)
+        A = g.normal(0, 1, (N, N))
+        B = g.normal(0, 0.5, (N, N, N, N))
+        h1 = (A + A.T) / 2
+        h2 = (B + B.transpose(1, 0, 3, 2) + B.transpose(2, 3, 0, 1) + B.transpose(3, 2, 1, 0)) / 4
+        v0 = inputs.device_state(N, ne, 10, torch.complex128)
+        dim = v0.numel()
+        row = {"amplitudes": dim}
+        for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+            v = v0.to(dt)
+            o = torch.empty_like(v)
+            f = lambda: fsgpu.apply_molecular_hamiltonian(v, h1, h2, N, ne, out=o, ctx=ctx)
+            f()
+            ms = _timed(f, steps=2)
+            flops = 2 * N * N * 3 * N * N * 2 * dim
+            row[name] = {"ms": ms, "gemm_tflops": flops / (ms / 1e3) / 1e12}
+            del v, o
+        res["norb%d_nelec%d_%d" % (N, ne[0], ne[1])] = row
+        del v0
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_small_rotation(args, ctx):

@@ -231,6 +231,23 @@ int fs_apply_quad_ham_evolution(fs_ctx *ctx, void *vec, int dtype, const double 
                                 const double *M_b, double t, int norb, int n_alpha, int n_beta,
                                 void *stream);
 
+/* ---- Operator action (operator-action section): out = H vec for the
+ * molecular Hamiltonian (the molecular Hamiltonian equation)
+ *   H = constant + sum_{pq sigma} h_pq a^dag_{p sigma} a_{q sigma}
+ *       + 1/2 sum_{pqrs sigma tau} h_pqrs a^dag_{p sigma} a^dag_{r tau} a_{s tau} a_{q sigma}
+ * with REAL tensors: one_body = h (N x N doubles), two_body = h_pqrs (N^4
+ * doubles, index ((p*N + q)*N + r)*N + s).  `vec` and `out` are distinct
+ * device states of the same sector and dtype; `vec` is read only, `out` is
+ * overwritten.  The work runs in blocks whose N^2-fold intermediates use at
+ * most `workspace_bytes` of scratch (0: min(8 GiB, a quarter of free
+ * memory)).  The contractions over the two-body tensor are cuBLAS GEMMs in
+ * the state's precision; everything else runs in the library's kernels.
+ * N <= 32.  Asynchronous on `stream`. */
+int fs_apply_molecular_hamiltonian(fs_ctx *ctx, const void *vec, void *out, int dtype,
+                                   const double *one_body, const double *two_body,
+                                   double constant, int64_t workspace_bytes, int norb,
+                                   int n_alpha, int n_beta, void *stream);
+
 /* ---- Trotter-Suzuki time evolution (Hamiltonian time evolution section).
  * exp(-i H time) vec ~ S_order(time / n_steps)^n_steps with
  *   S_0(t) = exp(-i H_L t) .. exp(-i H_1 t),

@@ -418,6 +418,7 @@ int fs_destroy(fs_ctx* ctx) {
     for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
     cudaFree(ctx->d_status);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    release_blas(ctx);
     delete ctx;
   });
 }
@@ -777,6 +778,29 @@ int fs_apply_quad_ham_evolution(fs_ctx* ctx, void* vec, int dtype, const double*
     RotProgram pa = decompose_adjacent(norb, Ua.data());
     RotProgram pb = M_b ? decompose_adjacent(norb, Ub.data()) : pa;
     rotate_any(ctx, sa, sb, vec, dtype, Ua, Ub, pa, pb, st);
+  });
+}
+
+// ------------------------------------------------------ operator action
+int fs_apply_molecular_hamiltonian(fs_ctx* ctx, const void* vec, void* out, int dtype,
+                                   const double* one_body, const double* two_body,
+                                   double constant, int64_t workspace_bytes, int norb, int na,
+                                   int nb, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, const_cast<void*>(vec), dtype, norb, na, nb);
+    check_sector(ctx, out, dtype, norb, na, nb);
+    FS_REQUIRE(out != vec, FS_ERR_ARG, "input and output must be distinct buffers");
+    FS_REQUIRE(one_body != nullptr && two_body != nullptr, FS_ERR_ARG, "null tensor");
+    FS_REQUIRE(std::isfinite(constant), FS_ERR_ARG, "constant must be finite");
+    FS_REQUIRE(workspace_bytes >= 0, FS_ERR_ARG, "workspace_bytes must be >= 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Space* sa = get_space(ctx, norb, na, st);
+    Space* sb = get_space(ctx, norb, nb, st);
+    molecular_hamiltonian(ctx, sa, sb, vec, out, dtype, one_body, two_body, constant,
+                          workspace_bytes, st);
   });
 }
 

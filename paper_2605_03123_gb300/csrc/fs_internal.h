@@ -143,6 +143,11 @@ struct Space {
   std::vector<TPass> tpass_h;
   std::vector<TRecord> trec_h;
   std::vector<uint8_t> rkey_h;
+  // single-excitation gather table (operator action), built on first use:
+  // per string t, ne = n(N-n)+n entries (pq = p*N+q, src = E_qp t | sign<<31)
+  uint16_t* gpq = nullptr;
+  uint32_t* gsrc = nullptr;
+  int ne = 0;
 };
 
 struct Scratch {
@@ -171,6 +176,7 @@ struct Ctx {
   // a graph (a capture cannot run on the legacy default stream); the graph
   // itself is launched on the caller's stream
   cudaStream_t capture_stream = nullptr;
+  void* blas = nullptr;  // cuBLAS handle (operator action), created on first use
   std::mutex mu;
 };
 
@@ -360,6 +366,13 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir,
 //   dJ_ab[p][q] += sum_{ij} W_ij occ_a(i)_p occ_b(j)_q
 //   dJ_aa[p][q] += 1/2 sum_{ij} W_ij (occ_a(i)_p occ_a(i)_q + occ_b(j)_p occ_b(j)_q)
 // dJ_aa, dJ_ab: device [norb][norb] FP64 accumulators.
+void build_gather_table(Space* sp, cudaStream_t st);
+// H vec for a molecular Hamiltonian with real tensors (operator action);
+// workspace_bytes bounds the intermediate blocks (0: automatic).
+void molecular_hamiltonian(Ctx* ctx, Space* sa, Space* sb, const void* vec, void* out, int dtype,
+                           const double* h1, const double* h2, double constant,
+                           int64_t workspace_bytes, cudaStream_t st);
+void release_blas(Ctx* ctx);
 // out = in^T for a [rows][cols] complex state (tiled, HBM-bound).
 void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
                       cudaStream_t st);

@@ -136,7 +136,56 @@ __global__ void k_exc_table(uint32_t* out, const uint32_t* masks, int64_t dim,
     }
 }
 
+// Gather table of the single excitations of each string t: for every
+// p in t and q not in t or q == p, in (p, q) order, the entry
+// pq = p * norb + q and src = E_qp t with sign bit 31 = the sign of
+// a^dag_q a_p |t> (equal to <t| a^dag_p a_q |src>).  ne = n(N - n) + n
+// entries per string.
+__global__ void k_gather_table(uint16_t* pq_out, uint32_t* src_out, const uint32_t* masks,
+                               int64_t dim, int norb, int ne) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= dim) return;
+  const uint32_t m = masks[t];
+  int k = 0;
+  for (int p = 0; p < norb; ++p) {
+    if (!((m >> p) & 1u)) continue;
+    for (int q = 0; q < norb; ++q) {
+      uint32_t v;
+      if (q == p) {
+        v = (uint32_t)t;
+      } else if (!((m >> q) & 1u)) {
+        const int lo = min(p, q), hi = max(p, q);
+        const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+        const uint32_t m2 = (m & ~(1u << p)) | (1u << q);
+        v = cns_rank(m2) | ((uint32_t)(__popc(m & between) & 1) << 31);
+      } else {
+        continue;
+      }
+      if (k < ne) {
+        pq_out[t * ne + k] = (uint16_t)(p * norb + q);
+        src_out[t * ne + k] = v;
+      }
+      ++k;
+    }
+  }
+}
+
 static int64_t choose(int n, int k) { return (int64_t)binom_host(n, k); }
+
+void build_gather_table(Space* sp, cudaStream_t st) {
+  if (sp->gpq) return;
+  const int n = sp->nocc, N = sp->norb;
+  sp->ne = n * (N - n) + n;
+  const size_t cnt = (size_t)sp->dim * std::max(sp->ne, 1);
+  FS_CUDA(cudaMalloc(&sp->gpq, cnt * sizeof(uint16_t)));
+  FS_CUDA(cudaMalloc(&sp->gsrc, cnt * sizeof(uint32_t)));
+  if (sp->ne > 0) {
+    k_gather_table<<<(unsigned)((sp->dim + 127) / 128), 128, 0, st>>>(sp->gpq, sp->gsrc,
+                                                                    sp->masks, sp->dim, N,
+                                                                    sp->ne);
+    FS_CUDA(cudaGetLastError());
+  }
+}
 
 Space* get_space(Ctx* ctx, int norb, int nocc, cudaStream_t st) {
   auto key = std::make_pair(norb, nocc);
@@ -191,6 +240,8 @@ void free_space(Space* s) {
   cudaFree(s->xcount);
   cudaFree(s->tpass);
   cudaFree(s->trec);
+  cudaFree(s->gpq);
+  cudaFree(s->gsrc);
   for (int b = 0; b < 4; ++b) {
     cudaFree(s->tgrec[b]);
     cudaFree(s->tgoff[b]);

@@ -67,6 +67,7 @@ SIGNATURES = {
                                               _I, _P],
     "fs_simulate_trotter_diag_coulomb": [_P, _P, _I, _P, _P, _P, _P, _D, _I, _I, _I, _I, _I,
                                          _P],
+    "fs_apply_molecular_hamiltonian": [_P, _P, _P, _I, _P, _P, _D, _I64, _I, _I, _I, _P],
     "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                       _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
 }
@@ -420,3 +421,24 @@ def simulate_trotter_diag_coulomb_(vec, one_body, J_aa, J_ab, time, norb, nelec,
     Jbb = None if J_bb is None else _f64(J_bb, (norb, norb))
     return _state_call("fs_simulate_trotter_diag_coulomb", vec, norb, nelec, ctx, _ptr(h),
                        _ptr(Ja), _ptr(Jb), _ptr(Jbb), float(time), int(n_steps), int(order))
+
+
+# ------------------------------------------------------ operator action
+def apply_molecular_hamiltonian(vec, one_body, two_body, norb, nelec, constant=0.0, out=None,
+                                workspace_bytes=0, ctx=None):
+    """H vec for the molecular Hamiltonian with real tensors h_pq, h_pqrs;
+    returns a new tensor (or fills `out`)."""
+    import torch
+    _check_state(vec, norb, nelec)
+    h1 = _f64(one_body, (norb, norb))
+    h2 = _f64(two_body, (norb, norb, norb, norb))
+    if out is None:
+        out = torch.empty_like(vec)
+    _check_state(out, norb, nelec)
+    if out.dtype != vec.dtype or out.data_ptr() == vec.data_ptr():
+        raise ValueError("out must be a distinct tensor of the same dtype")
+    ctx = ctx or context(vec.device.index)
+    _check("fs_apply_molecular_hamiltonian", load_library().fs_apply_molecular_hamiltonian(
+        ctx.handle, _P(vec.data_ptr()), _P(out.data_ptr()), _dtype_code(vec), _ptr(h1), _ptr(h2),
+        float(constant), int(workspace_bytes), norb, nelec[0], nelec[1], _stream_ptr()))
+    return out
