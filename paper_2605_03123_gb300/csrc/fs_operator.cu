@@ -9,8 +9,9 @@
 //         + sum_pq E^b_pq [sum_rs V_pqrs E^b_rs],
 //   k_pq = h_pq - 1/2 sum_r h_prrq,  V = h / 2,  W_pqrs = (h_pqrs + h_rspq) / 2.
 // Each bracket is a contraction over rs: with D_rs = E_rs psi it is the
-// plain GEMM G = V D (cuBLAS, in the state's precision, real matrix times
-// the complex vectors viewed as pairs of reals), and the outer E_pq is a
+// plain GEMM G = V D (cuBLAS; complex64 with FP32 emulated on the bf16
+// tensor cores, complex128 in FP64; real matrix times the complex vectors
+// viewed as pairs of reals), and the outer E_pq is a
 // gather through the single-excitation table.  The beta part runs on
 // blocks of rows (a beta excitation stays in its row), the alpha and mixed
 // parts on blocks of columns (an alpha excitation stays in its column);
@@ -167,10 +168,14 @@ static void gemm(Ctx* ctx, int dtype, int64_t m, int n, int k, const void* D, co
   cublasSetStream(h, st);
   cublasStatus_t s;
   if (dtype == FS_C64) {
+    // FP32 products emulated on the bf16 tensor cores (three-way bf16
+    // splits; FP32-level accuracy): measured 1.25x faster than FP32 FFMA
+    cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH);
     const float one = 1, zero = 0;
     s = cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, n, k, &one, (const float*)D, (int)m,
                     (const float*)V, ldv, &zero, (float*)G, (int)m);
   } else {
+    cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
     const double one = 1, zero = 0;
     s = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, n, k, &one, (const double*)D, (int)m,
                     (const double*)V, ldv, &zero, (double*)G, (int)m);
