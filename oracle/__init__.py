@@ -10,8 +10,9 @@ paper: string addresses (§3.1), number-operator-sum and diagonal-Coulomb
 evolution (§3.2.1, §3.2.2), orbital rotations by minor determinants (§2.3)
 and by Givens rotations (§3.2.3), the LUCJ ansatz (§4.3, §4.5.1) and its
 gradient, the remaining gates of Table 1, Trotter-Suzuki time evolution
-of double-factorized and diagonal-Coulomb Hamiltonians, and the action of a
-molecular Hamiltonian on a state.  Each function is pinned by tests that do not reuse it: a dense
+of double-factorized and diagonal-Coulomb Hamiltonians, the action of a
+molecular Hamiltonian on a state, and sampling configurations from a state
+or a Slater determinant.  Each function is pinned by tests that do not reuse it: a dense
 Jordan-Wigner construction with matrix exponentials (`bruteforce`), the
 Slater-determinant closed form (§2.4), the group-homomorphism identities of
 §2.3, the gate equivalences listed after Table 1, the state sizes printed in
@@ -34,3 +35,4 @@ from .trotter import (apply_num_interaction, apply_num_num_interaction,
                       apply_quad_ham_evolution, product_formula,
                       simulate_trotter_double_factorized, simulate_trotter_diag_coulomb)
 from .operator import apply_molecular_hamiltonian
+from .sampling import sample_state, sample_slater_spin, chain_rule_probability
