@@ -20,38 +20,58 @@
 import numpy as np
 
 
-def sample_state(vec, uniforms):
+def _margin(c, x, k):
+    """Distance from x to the nearer end of bin k of the cumulative sums c,
+    relative to the total: how far the uniform is from a decision boundary."""
+    lo = c[k - 1] if k > 0 else 0.0
+    return min(x - lo, c[k] - x) / c[-1]
+
+
+def sample_state(vec, uniforms, return_margin=False):
     """Addresses (row-major linear index into the (dim_a, dim_b) state) of the
-    samples for the given uniforms."""
+    samples for the given uniforms; with return_margin, also each shot's
+    distance to the nearest bin boundary, relative to the total."""
     p = np.abs(np.asarray(vec, dtype=complex).ravel()) ** 2
     c = np.cumsum(p)
     total = c[-1]
-    k = np.searchsorted(c, np.asarray(uniforms) * total, side="right")
-    return np.minimum(k, len(c) - 1)
+    x = np.asarray(uniforms) * total
+    k = np.minimum(np.searchsorted(c, x, side="right"), len(c) - 1)
+    if not return_margin:
+        return k
+    lo = np.where(k > 0, c[np.maximum(k - 1, 0)], 0.0)
+    return k, np.minimum(x - lo, c[k] - x) / total
 
 
 def _pick(weights, u):
     c = np.cumsum(weights)
     k = int(np.searchsorted(c, u * c[-1], side="right"))
-    return min(k, len(c) - 1)
+    k = min(k, len(c) - 1)
+    return k, _margin(c, u * c[-1], k)
 
 
-def sample_slater_spin(U, occ, uniforms):
-    """Masks of one spin's samples; uniforms has shape (shots, len(occ))."""
+def sample_slater_spin(U, occ, uniforms, return_margin=False):
+    """Masks of one spin's samples; uniforms has shape (shots, len(occ)).
+    With return_margin, also each shot's smallest distance (over its picks)
+    from a decision boundary, relative to that pick's total."""
     U = np.asarray(U, dtype=complex)
     occ = list(occ)
-    out = []
+    out, margins = [], []
     for us in np.atleast_2d(uniforms):
         V = U[:, occ].copy()
         mask = 0
+        m = np.inf
         for i in range(len(occ)):
             w = np.sum(np.abs(V) ** 2, axis=1)
-            p = _pick(w, us[i])
+            p, mi = _pick(w, us[i])
+            m = min(m, mi)
             mask |= 1 << p
             e = V[p] / np.linalg.norm(V[p])
             V = V - np.outer(V @ e.conj(), e)
         out.append(mask)
-    return np.array(out, dtype=np.int64)
+        margins.append(m)
+    if return_margin:
+        return np.array(out, dtype=object), np.array(margins)
+    return np.array(out, dtype=object)
 
 
 def chain_rule_probability(U, occ, order):
