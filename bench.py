@@ -340,6 +340,7 @@ def run_gpu(args):
             out["small_rotation"] = run_small_rotation(args, ctx)
             out["trotter"] = run_trotter(args, ctx)
             out["operator_action"] = run_operator_action(args, ctx)
+            out["sampling"] = run_sampling(args, ctx)
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -589,6 +590,60 @@ def run_operator_action(args, ctx):
         res["norb%d_nelec%d_%d" % (N, ne[0], ne[1])] = row
         del v0
         torch.cuda.empty_cache()
+    return res
+
+
+def run_sampling(args, ctx):
+    """Sampling configurations.  From the N=16 (8,8) state (1.66e8
+    amplitudes), 1e6 shots per call in complex64 and complex128: time per
+    call, samples/s, and the HBM fraction of the prefix pass, whose
+    algorithmic traffic is one read of the state.  From spinless Slater
+    determinants at 1/4 filling (the paper's Slater-sampling benchmark
+    shape), 1000 shots: time per call and the FP64 rate of the chain rule
+    (2 N n^2 FP64 FMA per shot)."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu, inputs
+    hbm, src = peaks()
+    shots = 1000000
+    res = {"state": {"workload": "norb16_nelec8_8", "shots": shots, "peak": src,
+                     "unit": "ms per call"}}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(77)
+    u = torch.rand(shots, dtype=torch.float64, device="cuda", generator=gen)
+    for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        v = inputs.device_state(NORB, NELEC, 12, dt)
+        S = v.numel() * v.element_size()
+        f = lambda: fsgpu.sample_state(v, NORB, NELEC, uniforms=u, ctx=ctx)
+        for _ in range(3):
+            f()
+        ctx.profile_start()
+        ms = _timed(f, steps=3)
+        prof = ctx.profile_stop()
+        cdf_ms = prof["sample_cdf"][1] / max(1, prof["sample_cdf"][0])
+        search_ms = prof["sample_search"][1] / max(1, prof["sample_search"][0])
+        gbs = S / (cdf_ms / 1e3) / 1e9
+        res["state"][name] = {"ms": ms, "samples_per_s": shots / (ms / 1e3),
+                              "cdf_ms": cdf_ms, "search_ms": search_ms,
+                              "cdf_gbs": gbs, "cdf_hbm_frac": gbs / hbm}
+        del v
+    del u
+    torch.cuda.empty_cache()
+    sl = {"unit": "ms per 1000 shots", "fp64_peak_tflops_nominal": 1.25}
+    for N in (64, 256, 1024):
+        n = N // 4
+        g = inputs.rng(2500 + N)
+        U = inputs.haar_unitary(N, g)
+        occ = list(range(n))
+        f = lambda: fsgpu.sample_slater(N, occ, U, shots=1000, seed=3, ctx=ctx)
+        f()
+        ctx.profile_start()
+        ms = _timed(f, steps=2)
+        prof = ctx.profile_stop()
+        kms = prof["slater_sample"][1] / max(1, prof["slater_sample"][0])
+        fma = 2.0 * N * n * n * 1000
+        sl["norb%d_nocc%d" % (N, n)] = {"ms": ms, "kernel_ms": kms,
+                                        "fp64_tflops": 2 * fma / (kms / 1e3) / 1e12}
+    res["slater"] = sl
     return res
 
 

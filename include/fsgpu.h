@@ -280,6 +280,44 @@ int fs_simulate_trotter_diag_coulomb(fs_ctx *ctx, void *vec, int dtype, const do
                                      const double *J_bb, double time, int n_steps, int order,
                                      int norb, int n_alpha, int n_beta, void *stream);
 
+/* ---- Sampling configurations.
+ *
+ * From a state (sample-based algorithms section: the probabilities are the
+ * squared magnitudes of the entries).  For shot k, with the uniform
+ * u_k = uniforms[k], out[k] is the first row-major address a = i * dim_b + j
+ * whose inclusive prefix sum_{a' <= a} |vec[a']|^2 exceeds u_k * ||vec||^2:
+ * the inverse of the cumulative distribution in address order, so each
+ * configuration is drawn with probability |vec[a]|^2 / ||vec||^2.  A
+ * configuration of zero amplitude is never returned.  uniforms: `shots`
+ * doubles in [0, 1) (device); values below 0 (and NaN) act as 0, values
+ * of 1 or more give the last configuration of nonzero amplitude.  out:
+ * `shots` int64 (device); every entry is -1 when ||vec||^2 is zero or not
+ * finite.  vec is read only.  Prefix sums run in FP64 for FS_C128 and in
+ * double-float pairs (about 48 significant bits) for FS_C64, so a uniform
+ * within about 1e-13 * ||vec||^2 of a boundary may land on either side of
+ * it.  Asynchronous on `stream`; the context's scratch holds the prefix
+ * tables (8 bytes per 256 amplitudes). */
+int fs_sample_state(fs_ctx *ctx, const void *vec, int dtype, int norb, int n_alpha, int n_beta,
+                    const double *uniforms, int64_t shots, int64_t *out, void *stream);
+
+/* From a Slater determinant (Slater-sampling section), one spin: the state
+ * U(U)|occ> has |amplitude|^2 = |det U[I, occ]|^2 (§2.4), a determinantal
+ * point process with kernel U[:, occ] U[:, occ]^dag.  Each shot picks nocc
+ * orbitals by the chain rule: at step i it takes orbital p with probability
+ * w_p / sum_q w_q, w_q being the squared norm of row q of U[:, occ] after
+ * projecting out the rows already picked, chosen by inverse CDF over the
+ * orbitals in increasing order with the uniform uniforms[k * nocc + i].
+ * U: host N x N complex (interleaved), of which only the columns listed in
+ * occ (host, nocc distinct orbitals) are read; they must be orthonormal to
+ * 1e-10 (FS_ERR_NOT_UNITARY otherwise).  uniforms: shots * nocc doubles in
+ * [0, 1) (device).  out: shots * ceil(norb / 64) words (device); bit p of
+ * word p / 64 of shot k is set when orbital p is occupied.  FP64
+ * throughout.  1 <= norb <= 1024.  Asynchronous on `stream`.  For both spins
+ * call once per spin with that spin's columns and uniforms: the spins are
+ * independent. */
+int fs_sample_slater(fs_ctx *ctx, const double *U, int norb, const int *occ, int nocc,
+                     const double *uniforms, int64_t shots, uint64_t *out, void *stream);
+
 /* Batched LUCJ (the ansatz of fs_lucj_forward, many independent circuits,
  * uneven sectors): ops[c], vecs[c], cots[c] describe circuit c exactly as
  * for fs_lucj_forward (and, when do_vjp, fs_lucj_vjp, which then follows

@@ -804,6 +804,69 @@ int fs_apply_molecular_hamiltonian(fs_ctx* ctx, const void* vec, void* out, int 
   });
 }
 
+// ------------------------------------------------------------ sampling
+int fs_sample_state(fs_ctx* ctx, const void* vec, int dtype, int norb, int na, int nb,
+                    const double* uniforms, int64_t shots, int64_t* out, void* stream) {
+  return guarded([&] {
+    check_sector(ctx, const_cast<void*>(vec), dtype, norb, na, nb);
+    FS_REQUIRE(shots >= 0, FS_ERR_ARG, "shots must be >= 0");
+    FS_REQUIRE(shots == 0 || (uniforms != nullptr && out != nullptr), FS_ERR_ARG,
+               "null uniforms or output");
+    FS_REQUIRE(((uintptr_t)uniforms & 7u) == 0 && ((uintptr_t)out & 7u) == 0, FS_ERR_ARG,
+               "uniforms and output must be 8-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = get_space(ctx, norb, na, st)->dim * get_space(ctx, norb, nb, st)->dim;
+    sample_state(ctx, vec, dtype, n, uniforms, shots, out, st);
+  });
+}
+
+int fs_sample_slater(fs_ctx* ctx, const double* U, int norb, const int* occ, int nocc,
+                     const double* uniforms, int64_t shots, uint64_t* out, void* stream) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    FS_REQUIRE(norb >= 1 && norb <= 1024, FS_ERR_ARG, "norb must be in [1, 1024]");
+    FS_REQUIRE(nocc >= 0 && nocc <= norb, FS_ERR_ARG, "nocc must be in [0, norb]");
+    FS_REQUIRE(U != nullptr && (nocc == 0 || occ != nullptr), FS_ERR_ARG,
+               "null matrix or occupation list");
+    FS_REQUIRE(shots >= 0, FS_ERR_ARG, "shots must be >= 0");
+    FS_REQUIRE(shots == 0 || ((nocc == 0 || uniforms != nullptr) && out != nullptr), FS_ERR_ARG,
+               "null uniforms or output");
+    FS_REQUIRE(((uintptr_t)uniforms & 7u) == 0 && ((uintptr_t)out & 7u) == 0, FS_ERR_ARG,
+               "uniforms and output must be 8-byte aligned");
+    std::vector<char> seen(norb, 0);
+    for (int k = 0; k < nocc; ++k) {
+      FS_REQUIRE(occ[k] >= 0 && occ[k] < norb, FS_ERR_ARG, "occupied orbital out of range");
+      FS_REQUIRE(!seen[occ[k]], FS_ERR_ARG, "occupied orbitals must be distinct");
+      seen[occ[k]] = 1;
+    }
+    // Phi = U[:, occ]; its columns must be orthonormal (Phi^dag Phi = I)
+    std::vector<zd> Phi((size_t)norb * (nocc > 0 ? nocc : 1));
+    for (int p = 0; p < norb; ++p)
+      for (int j = 0; j < nocc; ++j) {
+        const size_t k = (size_t)p * norb + occ[j];
+        Phi[(size_t)p * nocc + j] = zd(U[2 * k], U[2 * k + 1]);
+      }
+    double err = 0;
+    for (int a = 0; a < nocc; ++a)
+      for (int b = a; b < nocc; ++b) {
+        zd g = 0;
+        for (int p = 0; p < norb; ++p)
+          g += std::conj(Phi[(size_t)p * nocc + a]) * Phi[(size_t)p * nocc + b];
+        err = std::max(err, std::abs(g - (a == b ? 1.0 : 0.0)));
+      }
+    FS_REQUIRE(std::isfinite(err) && err <= 1e-10, FS_ERR_NOT_UNITARY,
+               "the occupied columns of U are not orthonormal (max |Phi^dag Phi - I| = " +
+                   std::to_string(err) + ")");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    current_ctx() = ctx;
+    FS_CUDA(cudaSetDevice(ctx->device));
+    sample_slater(ctx, Phi, norb, nocc, uniforms, shots, out, (cudaStream_t)stream);
+  });
+}
+
 // ------------------------------------------------------------ Trotter
 static void trotter_checks(double time, int n_steps, int order) {
   FS_REQUIRE(std::isfinite(time), FS_ERR_ARG, "time must be finite");

@@ -373,6 +373,14 @@ void molecular_hamiltonian(Ctx* ctx, Space* sa, Space* sb, const void* vec, void
                            const double* h1, const double* h2, double constant,
                            int64_t workspace_bytes, cudaStream_t st);
 void release_blas(Ctx* ctx);
+// Configurations drawn from |vec|^2 by inverse CDF in address order, for
+// `shots` device uniforms; n = dim_a * dim_b amplitudes.
+void sample_state(Ctx* ctx, const void* vec, int dtype, int64_t n, const double* u,
+                  int64_t shots, int64_t* out, cudaStream_t st);
+// Occupation masks (words of 64 bits per shot) of one spin of a Slater
+// determinant with occupied columns Phi (N x n, row-major, orthonormal).
+void sample_slater(Ctx* ctx, const std::vector<zd>& Phi, int N, int n, const double* u,
+                   int64_t shots, uint64_t* out, cudaStream_t st);
 // out = in^T for a [rows][cols] complex state (tiled, HBM-bound).
 void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
                       cudaStream_t st);

@@ -68,6 +68,8 @@ SIGNATURES = {
     "fs_simulate_trotter_diag_coulomb": [_P, _P, _I, _P, _P, _P, _P, _D, _I, _I, _I, _I, _I,
                                          _P],
     "fs_apply_molecular_hamiltonian": [_P, _P, _P, _I, _P, _P, _D, _I64, _I, _I, _I, _P],
+    "fs_sample_state": [_P, _P, _I, _I, _I, _I, _P, _I64, _P, _P],
+    "fs_sample_slater": [_P, _P, _I, _P, _I, _P, _I64, _P, _P],
     "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                       _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
 }
@@ -442,3 +444,84 @@ def apply_molecular_hamiltonian(vec, one_body, two_body, norb, nelec, constant=0
         ctx.handle, _P(vec.data_ptr()), _P(out.data_ptr()), _dtype_code(vec), _ptr(h1), _ptr(h2),
         float(constant), int(workspace_bytes), norb, nelec[0], nelec[1], _stream_ptr()))
     return out
+
+
+# ------------------------------------------------------------- sampling
+def _uniforms(uniforms, count, seed, device):
+    """FP64 uniforms on the device: the given ones, or `count` drawn from a
+    torch generator seeded with `seed`."""
+    import torch
+    if uniforms is not None:
+        if isinstance(uniforms, torch.Tensor):
+            u = uniforms.to(device=device, dtype=torch.float64)
+        else:
+            u = torch.from_numpy(np.ascontiguousarray(uniforms, dtype=np.float64)).to(device)
+        return u.contiguous()
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.rand(count, dtype=torch.float64, device=device, generator=g)
+
+
+def sample_state(vec, norb, nelec, shots=None, uniforms=None, seed=0, ctx=None):
+    """Addresses a = i * dim_b + j (int64 CUDA tensor) of configurations drawn
+    from |vec|^2 by inverse CDF in address order, one per uniform (FP64 in
+    [0, 1), given or drawn from a seeded generator)."""
+    import torch
+    _check_state(vec, norb, nelec)
+    if uniforms is None and shots is None:
+        raise ValueError("give shots or uniforms")
+    u = _uniforms(uniforms, shots, seed, vec.device).reshape(-1)
+    out = torch.empty(u.numel(), dtype=torch.int64, device=vec.device)
+    ctx = ctx or context(vec.device.index)
+    _check("fs_sample_state", load_library().fs_sample_state(
+        ctx.handle, _P(vec.data_ptr()), _dtype_code(vec), norb, nelec[0], nelec[1],
+        _P(u.data_ptr()), u.numel(), _P(out.data_ptr()), _stream_ptr()))
+    return out
+
+
+def addresses_to_strings(addr, norb, nelec, ctx=None):
+    """(alpha masks, beta masks) of sampled addresses, from the library's
+    string tables."""
+    ma, mb = string_table(norb, nelec[0], ctx), string_table(norb, nelec[1], ctx)
+    a = addr.cpu().numpy() if hasattr(addr, "cpu") else np.asarray(addr)
+    return ma[a // len(mb)], mb[a % len(mb)]
+
+
+def _slater_spin(U, occ, norb, shots, uniforms, seed, device, ctx):
+    import torch
+    occ = np.ascontiguousarray(occ, dtype=np.int32).reshape(-1)
+    Um = _f64(U, (norb, norb), True)
+    n = occ.size
+    if uniforms is None and shots is None:
+        raise ValueError("give shots or uniforms")
+    u = _uniforms(uniforms, (shots or 0) * n, seed, device).reshape(-1)
+    if n and u.numel() % n:
+        raise ValueError("uniforms must have shape (shots, len(occ))")
+    shots = u.numel() // n if n else int(shots)
+    words = (norb + 63) // 64
+    out = torch.empty(max(shots * words, 1), dtype=torch.int64, device=device)
+    _check("fs_sample_slater", load_library().fs_sample_slater(
+        ctx.handle, _ptr(Um), norb, _ptr(occ) if n else None, n,
+        _P(u.data_ptr()) if u.numel() else None, shots, _P(out.data_ptr()), _stream_ptr()))
+    m = out[:shots * words].cpu().numpy().view(np.uint64).reshape(shots, words)
+    return m[:, 0] if words == 1 else m
+
+
+def sample_slater(norb, occ, U, shots=None, uniforms=None, seed=0, device=None, ctx=None):
+    """Occupation masks (uint64 per shot; rows of ceil(norb/64) words when
+    norb > 64) sampled from the Slater determinant U(U)|occ>.  Spinless:
+    occ is a list of orbitals.  Spinful: occ = (occ_a, occ_b), U one matrix
+    or a pair (U_a, U_b), uniforms None or a pair; returns (masks_a,
+    masks_b), the spins drawn independently."""
+    import torch
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    device = torch.device(device)
+    ctx = ctx or context(device.index or 0)
+    spinful = len(occ) == 2 and not np.isscalar(occ[0])
+    if not spinful:
+        return _slater_spin(U, occ, norb, shots, uniforms, seed, device, ctx)
+    Us = U if (isinstance(U, (tuple, list)) and len(U) == 2) else (U, U)
+    us = uniforms if uniforms is not None else (None, None)
+    return tuple(_slater_spin(Us[s], occ[s], norb, shots, us[s], seed + s, device, ctx)
+                 for s in range(2))
