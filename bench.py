@@ -593,7 +593,18 @@ def run_operator_action(args, ctx):
     return res
 
 
-def run_sampling(args, ctx):
+def run_sampling_only(args):
+    """Profiling only: the sampling section alone, at the sector given by
+    --norb/--nalpha/--nbeta (default the N=16 (8,8) workload)."""
+    from paper_2605_03123_gb300 import fsgpu
+    global NORB, NELEC
+    if args.norb:
+        NORB, NELEC = args.norb, (args.nalpha, args.nbeta)
+    fsgpu.load_library()
+    print(json.dumps(run_sampling(args, fsgpu.context(0), slater=not args.norb)))
+
+
+def run_sampling(args, ctx, slater=True):
     """Sampling configurations.  From the N=16 (8,8) state (1.66e8
     amplitudes), 1e6 shots per call in complex64 and complex128: time per
     call, samples/s, and the HBM fraction of the prefix pass, whose
@@ -604,8 +615,9 @@ def run_sampling(args, ctx):
     import torch
     from paper_2605_03123_gb300 import fsgpu, inputs
     hbm, src = peaks()
-    shots = 1000000
-    res = {"state": {"workload": "norb16_nelec8_8", "shots": shots, "peak": src,
+    shots = args.shots
+    res = {"state": {"workload": "norb%d_nelec%d_%d" % (NORB, NELEC[0], NELEC[1]),
+                     "shots": shots, "peak": src,
                      "unit": "ms per call"}}
     gen = torch.Generator(device="cuda")
     gen.manual_seed(77)
@@ -628,6 +640,8 @@ def run_sampling(args, ctx):
         del v
     del u
     torch.cuda.empty_cache()
+    if not slater:
+        return res
     sl = {"unit": "ms per 1000 shots", "fp64_peak_tflops_nominal": 1.25}
     for N in (64, 256, 1024):
         n = N // 4
@@ -773,8 +787,14 @@ def main():
     ap.add_argument("--nalpha", type=int, default=0)
     ap.add_argument("--nbeta", type=int, default=0)
     ap.add_argument("--layers", type=int, default=NLAYERS)
+    ap.add_argument("--shots", type=int, default=1000000,
+                    help="shots per call of the state-sampling section")
+    ap.add_argument("--sampling-only", action="store_true",
+                    help="profiling only: the sampling section alone")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sampling_only:
+        run_sampling_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
