@@ -84,13 +84,26 @@ template <> struct Acc<float> {
     const dfl s = two_sum(h1, h2);
     return fast_two_sum(s.h, s.l + (l1 + l2));
   }
-  // u * a for a uniform u given in FP64 (u split into two floats)
-  static __device__ __forceinline__ T scale(double u, T a) {
-    const float uh = (float)u;
-    const float ul = (float)(u - (double)uh);
+  // u * a for a uniform u = uh + ul split into two floats
+  static __device__ __forceinline__ T scale(float uh, float ul, T a) {
     const float p = uh * a.h;
     const float e = fmaf(uh, a.h, -p) + (uh * a.l + ul * a.h);
     return fast_two_sum(p, e);
+  }
+  // the uniform of a shot, read and split on lane 0 only (FP64 issue is
+  // scarce on GB300), then broadcast; NaN reads as 0
+  static __device__ __forceinline__ void uniform(const double* u, int64_t s, int lane,
+                                                 float& uh, float& ul) {
+    float h = 0.f, l = 0.f;
+    if (lane == 0) {
+      const double x = u[s];
+      if (x == x) {
+        h = (float)x;
+        l = (float)(x - (double)h);
+      }
+    }
+    uh = __shfl_sync(0xffffffffu, h, 0);
+    ul = __shfl_sync(0xffffffffu, l, 0);
   }
   static __device__ __forceinline__ T shfl_up(T a, int d) {
     return dfl{__shfl_up_sync(0xffffffffu, a.h, d), __shfl_up_sync(0xffffffffu, a.l, d)};
@@ -110,7 +123,13 @@ template <> struct Acc<double> {
   static __device__ __forceinline__ bool pos(T a) { return a > 0.0; }
   static __device__ __forceinline__ bool finite(T a) { return isfinite(a); }
   static __device__ __forceinline__ T prob(double2 z) { return fma(z.x, z.x, z.y * z.y); }
-  static __device__ __forceinline__ T scale(double u, T a) { return u * a; }
+  static __device__ __forceinline__ T scale(double u, double, T a) { return u * a; }
+  static __device__ __forceinline__ void uniform(const double* u, int64_t s, int, double& uh,
+                                                 double& ul) {
+    const double x = u[s];
+    uh = x == x ? x : 0.0;
+    ul = 0.0;
+  }
   static __device__ __forceinline__ T shfl_up(T a, int d) {
     return __shfl_up_sync(0xffffffffu, a, d);
   }
@@ -275,8 +294,9 @@ __global__ void __launch_bounds__(256)
       if (lane == 0) out[s] = -1;
       continue;
     }
-    const double us = u[s];
-    T x = A::scale(us == us ? us : 0.0, total);
+    R uh, ul;
+    A::uniform(u, s, lane, uh, ul);
+    T x = A::scale(uh, ul, total);
     if (!A::pos(x)) x = A::zero();
     bool ge = false;
     if (!A::gt(total, x)) {
@@ -304,9 +324,27 @@ __global__ void __launch_bounds__(256)
     const int cnt = left <= 0 ? 0 : (left >= 8 ? 8 : (int)left);
     T p[8];
     T own = A::zero();
+    cx_t<R> z[8];
+    if (cnt == 8) {
+      if constexpr (sizeof(R) == 4) {
+        const float4* p4 = reinterpret_cast<const float4*>(v + a0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 q = p4[k];
+          z[2 * k] = make_float2(q.x, q.y);
+          z[2 * k + 1] = make_float2(q.z, q.w);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) z[k] = v[a0 + k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z[k] = k < cnt ? v[a0 + k] : cx_t<R>{};
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      p[k] = k < cnt ? A::prob(v[a0 + k]) : A::zero();
+      p[k] = k < cnt ? A::prob(z[k]) : A::zero();
       own = A::add(own, p[k]);
     }
     T incl = own;
