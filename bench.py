@@ -166,6 +166,22 @@ def algorithmic_flops(kernel, norb, nelec, amplitudes):
     return per * amplitudes
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The job's time: the largest of the ranks' times (ms).  Each rank runs
+    its own replica; the job ends when the slowest rank ends."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_gpu(args):
     import torch
     from paper_2605_03123_gb300 import fsgpu
@@ -215,13 +231,9 @@ def run_gpu(args):
         prof = ctx.profile_stop()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * NLAYERS * args.steps / (ms / 1e3)
+    value = job_throughput(world, NLAYERS * args.steps, ms)
     launches = sum(v[2] for v in prof.values())
 
     # parity at full size, properties: recovered input and dL/dpsi_in identities
@@ -252,9 +264,9 @@ def run_gpu(args):
             step_e2e()
         b.record()
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b) / args.e2e_steps
+        ems = max_over_ranks(a.elapsed_time(b) / args.e2e_steps, dist, "cuda")
         grad_bytes = K.size * 16 + Jaa.size * 8 + Jab.size * 8
-        e2e = {"value": world * NLAYERS / (ems / 1e3), "unit": "layers/s",
+        e2e = {"value": job_throughput(world, NLAYERS, ems), "unit": "layers/s",
                "h2d_bytes_per_step": 2 * S, "d2h_bytes_per_step": S + grad_bytes,
                "ms_per_step": ems}
 
