@@ -205,6 +205,8 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
     for (int p = 0; p < N; ++p)
       if (p < a || p >= a + W) out.push_back(p);
     const int no = (int)out.size();
+    std::vector<std::vector<uint32_t>> cls(W);
+    std::vector<std::vector<uint8_t>> ckey(W);
     for (int m = 1; m < W; ++m) {
       const int ne = n - m;
       if (ne < 0 || ne > no) continue;
@@ -226,12 +228,32 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
             }
             ++k;
           }
-        orbits.push_back((uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
-        okey.push_back((uint8_t)top3_group(omask, N));
+        cls[m].push_back((uint32_t)ro | ((uint32_t)clo << 16) | ((uint32_t)m << 24));
+        ckey[m].push_back((uint8_t)top3_group(omask, N));
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), r = x + c;
         x = (((r ^ x) >> 2) / c) | r;
         if (x >> no) break;
+      }
+    }
+    // Classes in descending order of Givens work per orbit (pairs per
+    // rotation C(W-2, m-1), then strings C(W, m)), each padded with empty
+    // descriptors (m = 0, skipped by the kernels) to a multiple of 32, so
+    // that no warp holds two classes (divergent paths run one after the
+    // other) and the per-warp work of a window step is even.
+    std::vector<int> order;
+    for (int m = 1; m < W; ++m) order.push_back(m);
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+      const uint64_t pu = C(W - 2, u - 1), pv = C(W - 2, v - 1);
+      return pu != pv ? pu > pv : C(W, u) > C(W, v);
+    });
+    for (int m : order) {
+      if (cls[m].empty()) continue;
+      orbits.insert(orbits.end(), cls[m].begin(), cls[m].end());
+      okey.insert(okey.end(), ckey[m].begin(), ckey[m].end());
+      while ((orbits.size() - off[a]) % 32) {
+        orbits.push_back(0u);
+        okey.push_back(0);
       }
     }
 
@@ -375,6 +397,8 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
     for (int p = 0; p < N; ++p)
       if (!((qmask >> p) & 1u)) out.push_back(p);
     const int no = (int)out.size();
+    std::vector<TRecord> rcls[5];
+    std::vector<uint8_t> rck[5];
     for (int m = 1; m <= 4; ++m) {
       const int ne = n - m;
       if (ne < 0 || ne > no) continue;
@@ -400,12 +424,24 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
           g |= (uint8_t)(acc << (j + 1));  // bit j+1: parity of O before q_{j+1}
         }
         r.gbits = g;
-        recs.push_back(r);
-        rkey.push_back((uint8_t)top3_group(omask, N));
+        rcls[m].push_back(r);
+        rck[m].push_back((uint8_t)top3_group(omask, N));
         if (ne == 0) break;
         uint64_t c = x & (~x + 1), rr = x + c;
         x = (((rr ^ x) >> 2) / c) | rr;
         if (x >> no) break;
+      }
+    }
+    // Classes in descending order of work per record (terms of the local
+    // pairs: 36, 24, 16, 4 for m = 2, 3, 1, 4), each padded with empty
+    // records (m = 0, skipped by the kernels) to a multiple of 32.
+    for (int m : {2, 3, 1, 4}) {
+      if (rcls[m].empty()) continue;
+      recs.insert(recs.end(), rcls[m].begin(), rcls[m].end());
+      rkey.insert(rkey.end(), rck[m].begin(), rck[m].end());
+      while ((recs.size() - ps.rec0) % 32) {
+        recs.push_back(TRecord{});
+        rkey.push_back(0);
       }
     }
     ps.rec1 = (int)recs.size();
@@ -414,9 +450,16 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
 
 // Regrouping of an item list for clusters of 2^b CTAs: within each segment
 // [seg[i], seg[i + 1]) the items are stably reordered by their top-b group
-// key >> (3 - b) (keeping the m order inside a group); gofs[i * 9 + r] is the
+// key >> (3 - b) (keeping the class order inside a group, each class of a
+// group padded to a multiple of 32 again);
+// gofs[i * 9 + r] is the
 // start of group r of segment i (r = 0 .. 2^b, the last entry the segment
 // end).
+static bool is_padding(uint32_t orbit) { return (orbit >> 24) == 0; }
+static bool is_padding(const TRecord& r) { return r.m == 0; }
+static int item_class(uint32_t orbit) { return (int)(orbit >> 24); }
+static int item_class(const TRecord& r) { return r.m; }
+
 template <typename T>
 static void regroup(const std::vector<T>& items, const std::vector<uint8_t>& key,
                     const std::vector<int>& seg, int b, std::vector<T>& out,
@@ -427,9 +470,18 @@ static void regroup(const std::vector<T>& items, const std::vector<uint8_t>& key
   gofs.assign((size_t)std::max(ns, 0) * 9, 0);
   for (int i = 0; i < ns; ++i) {
     for (int r = 0; r < G; ++r) {
-      gofs[(size_t)i * 9 + r] = (int)out.size();
-      for (int k = seg[i]; k < seg[i + 1]; ++k)
-        if ((key[k] >> (3 - b)) == r) out.push_back(items[k]);
+      const size_t g0 = out.size();
+      gofs[(size_t)i * 9 + r] = (int)g0;
+      int cur = -1;
+      for (int k = seg[i]; k < seg[i + 1]; ++k) {
+        if ((key[k] >> (3 - b)) != r || is_padding(items[k])) continue;
+        if (item_class(items[k]) != cur) {  // a new class starts on a warp
+          while ((out.size() - g0) % 32) out.push_back(T{});
+          cur = item_class(items[k]);
+        }
+        out.push_back(items[k]);
+      }
+      while ((out.size() - g0) % 32) out.push_back(T{});
     }
     for (int r = G; r <= 8; ++r) gofs[(size_t)i * 9 + r] = (int)out.size();
   }

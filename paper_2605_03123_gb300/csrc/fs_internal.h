@@ -58,7 +58,9 @@ struct WinStep {
 std::vector<WinStep> schedule_windows(const RotProgram& rp, int N, int W);
 // Orbit tables of the strings of n electrons in N orbitals for windows of W
 // adjacent orbitals: for each window position a, orbits[off[a] .. off[a+1])
-// hold R_O | c_lo << 16 | m << 24 sorted by m, okey[i] is the occupation of
+// hold R_O | c_lo << 16 | m << 24 grouped by m (classes in descending order
+// of work, each padded with empty descriptors, m = 0, to a multiple of 32),
+// okey[i] is the occupation of
 // the top three orbitals in orbit i's outside configuration (a 3-bit
 // number), and offs[((a * (n+1) + c_lo) << W) + S] is the in-window rank
 // offset.
@@ -67,7 +69,8 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
                         std::vector<uint8_t>& okey);
 // The orbits regrouped for clusters of 2^b CTAs: per window position a,
 // group r (occupation of the top b orbitals, the strings of cluster rank r)
-// at gorb[goff[a * 9 + r] .. goff[a * 9 + r + 1]), sorted by m inside.
+// at gorb[goff[a * 9 + r] .. goff[a * 9 + r + 1]), class order kept inside,
+// without the padding.
 void window_groups_host(const std::vector<uint32_t>& orbits, const std::vector<int>& off,
                         const std::vector<uint8_t>& okey, int b, std::vector<uint32_t>& gorb,
                         std::vector<int>& goff);
@@ -80,7 +83,9 @@ struct TPassDev {
 };
 // Transition-reduction passes (see tpass_tables_host): a subset of four
 // orbitals q[0] < .. < q[3], the local slots (i*4 + j <-> E_{q_i q_j}) this
-// pass owns, and its orbit records recs[rec0 .. rec1) sorted by m.
+// pass owns, and its orbit records recs[rec0 .. rec1) grouped by m (classes
+// in descending order of work, each padded with empty records to a multiple
+// of 32).
 struct TPass {
   int q[4];
   uint32_t keep;
@@ -97,7 +102,8 @@ struct alignas(16) TRecord {
 void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
                        std::vector<TRecord>& recs, std::vector<uint8_t>& rkey);
 // The records regrouped for clusters of 2^b CTAs: per pass i, group r at
-// grec[goff[i * 9 + r] .. goff[i * 9 + r + 1]), sorted by m inside.
+// grec[goff[i * 9 + r] .. goff[i * 9 + r + 1]), class order kept inside,
+// without the padding.
 void tpass_groups_host(const std::vector<TPass>& passes, const std::vector<TRecord>& recs,
                        const std::vector<uint8_t>& rkey, int b, std::vector<TRecord>& grec,
                        std::vector<int>& goff);
@@ -118,7 +124,8 @@ struct Space {
   int* xcount = nullptr;       // [norb*norb] actual entries per list
   // window tables for the register-blocked sweeps, per window width W:
   // orbit descriptors R_O | c_lo << 16 | m << 24 grouped by window position
-  // and sorted by m, and in-window rank offsets F[a][c_lo][S]
+  // and grouped by m (padded per class), and in-window rank offsets
+  // F[a][c_lo][S]
   struct Win {
     uint32_t* orbits = nullptr;
     int* off = nullptr;
@@ -307,7 +314,7 @@ struct SweepGeom {
   const TRecord* trec;
   int npass;
   // window tables of the rotated spin (window kernels only)
-  const uint32_t* orbits;  // per window position, orbit descriptors sorted by m
+  const uint32_t* orbits;  // per window position, orbit descriptors grouped by m
   const int* orb_off;      // [npos + 1] start of each position's list
   // blocked clusters: orbits regrouped by cluster rank, rank r's orbits of
   // position a at orb_grp[orb_goff[a * 9 + r] .. orb_goff[a * 9 + r + 1]);

@@ -283,6 +283,26 @@ __device__ __forceinline__ R warp_transpose_sum(R (&v)[32], int lane) {
   return v[0];
 }
 
+// Items [lo, hi) (classes of equal work, in descending order of work, each
+// a multiple of 32 long) are dealt in chunks of 32: chunk c goes to cluster
+// rank c % cs, and a rank's chunks go to its NT / 32 warps round by round,
+// in warp order on even rounds and in reverse order on odd rounds, so the
+// work evens out over ranks and warps and no warp mixes two classes.
+// Item of round R for thread t of rank `rank`, or -1 past the end; rounds
+// run while dealt_round<NT>(lo, hi, R, rank, cs).
+template <int NT>
+__device__ __forceinline__ int dealt_item(int lo, int hi, int R, int t, int rank, int cs) {
+  constexpr int NW = NT / 32;
+  const int w = t >> 5;
+  const int k = R * NW + ((R & 1) ? NW - 1 - w : w);
+  const int o = lo + 32 * (rank + cs * k) + (t & 31);
+  return o < hi ? o : -1;
+}
+template <int NT>
+__device__ __forceinline__ bool dealt_round(int lo, int hi, int R, int rank, int cs) {
+  return lo + 32 * (rank + cs * R * (NT / 32)) < hi;
+}
+
 template <typename R, int W, bool WIN>
 struct ProgOf {
   using type = GProg<R>;
@@ -467,7 +487,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       const int ga = prog.g0[st], gb = prog.g0[st + 1];
       const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
       const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
-      int lo = o0, hi = o1;
+      int lo = o0, hi = o1, drank = 0, dcs = 1;
       const uint32_t* olist = g.orbits;
       if constexpr (CS > 1) {
         if (g.blocked && a + W <= g.norb - g.lgcs) {
@@ -475,12 +495,13 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
           lo = __ldg(g.orb_goff + a * 9 + rank);
           hi = __ldg(g.orb_goff + a * 9 + rank + 1);
         } else {
-          const int per = (o1 - o0 + CS - 1) / CS;
-          lo = o0 + rank * per;
-          hi = min(o1, lo + per);
+          drank = rank;
+          dcs = CS;
         }
       }
-      for (int o = lo + ltid; o < hi; o += HT) {
+      for (int rd = 0; dealt_round<HT>(lo, hi, rd, drank, dcs); ++rd) {
+        const int o = dealt_item<HT>(lo, hi, rd, ltid, drank, dcs);
+        if (o < 0) continue;
         const uint32_t desc = __ldg(olist + o);
         switch (desc >> 24) {
           case 1: win_orbit<R, CS, 1, W, 1>(desc, F, bs, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
@@ -503,19 +524,19 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       const int ga = prog.g0[st], gb = prog.g0[st + 1];
       const int o0 = g.orb_off[a], o1 = g.orb_off[a + 1];
       const uint16_t* F = g.offs + (size_t)a * g.offs_stride;
-      int lo, hi;
+      int lo = o0, hi = o1, drank = rank, dcs = CS;
       const uint32_t* olist = g.orbits;
       if (CS > 1 && g.blocked && a + W <= g.norb - g.lgcs) {
         // window clear of the top orbitals: this rank's own orbits
         olist = g.orb_grp;
         lo = __ldg(g.orb_goff + a * 9 + rank);
         hi = __ldg(g.orb_goff + a * 9 + rank + 1);
-      } else {
-        const int per = (o1 - o0 + CS - 1) / CS;
-        lo = o0 + rank * per;
-        hi = min(o1, lo + per);
+        drank = 0;
+        dcs = 1;
       }
-      for (int o = lo + tid; o < hi; o += kThreads) {
+      for (int rd = 0; dealt_round<kThreads>(lo, hi, rd, drank, dcs); ++rd) {
+        const int o = dealt_item<kThreads>(lo, hi, rd, tid, drank, dcs);
+        if (o < 0) continue;
         const uint32_t desc = __ldg(olist + o);
         switch (desc >> 24) {
           case 1: win_orbit<R, CS, NST, W, 1>(desc, F, base, st_stride, cbr, KV, kv_eff, prog, ga, gb); break;
@@ -590,19 +611,19 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         R acc[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = 0;
-        int lo, hi;
+        int lo = pd.rec0, hi = pd.rec1, drank = rank, dcs = CS;
         const TRecord* rlist = g.trec;
         if (CS > 1 && g.blocked && pd.q[3] < g.norb - g.lgcs) {
           // subset clear of the top orbitals: this rank's own records
           rlist = g.trec_grp;
           lo = __ldg(g.tgoff + ip * 9 + rank);
           hi = __ldg(g.tgoff + ip * 9 + rank + 1);
-        } else {
-          const int per = (pd.rec1 - pd.rec0 + CS - 1) / CS;
-          lo = pd.rec0 + rank * per;
-          hi = min(pd.rec1, lo + per);
+          drank = 0;
+          dcs = 1;
         }
-        for (int o = lo + tid; o < hi; o += kThreads) {
+        for (int rd = 0; dealt_round<kThreads>(lo, hi, rd, drank, dcs); ++rd) {
+          const int o = dealt_item<kThreads>(lo, hi, rd, tid, drank, dcs);
+          if (o < 0) continue;
           TRecord rc;
           *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(rlist + o));
           switch (rc.m) {
