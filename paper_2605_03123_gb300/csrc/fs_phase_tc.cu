@@ -72,6 +72,30 @@ __global__ void __launch_bounds__(256)
   const int nkw = nk >> 1;  // 32-bit words of bf16 pairs per column
 #pragma unroll 1
   for (int nt = 0; nt < kTcCols / 8; ++nt) {
+    // lane holds rows (g, g+8), columns 2t, 2t+1 of the n-tile; the two
+    // columns move as one 16-byte access when the row allows it.  The state
+    // and the beta factors are loaded before the contraction so that their
+    // latency overlaps it.
+    const int64_t jj = j0 + 8 * nt + 2 * t;
+    float2 v[2][2], fb[2];
+    bool pair[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) fb[c] = jj + c < db ? ea_b[jj + c] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t r = h ? r1 : r0;
+      const float2* p = vec + (r < da ? r : 0) * db + jj;
+      pair[h] = r < da && jj + 1 < db && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0);
+      if (pair[h]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[h][0] = make_float2(q.x, q.y);
+        v[h][1] = make_float2(q.z, q.w);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          v[h][c] = (r < da && jj + c < db) ? p[c] : make_float2(0.f, 0.f);
+      }
+    }
     const int64_t jc = j0 + 8 * nt + g;  // column of this lane's B fragment
     float z[4] = {0.f, 0.f, 0.f, 0.f};
     for (int kb = 0; kb < nk; kb += 16) {
@@ -83,42 +107,34 @@ __global__ void __launch_bounds__(256)
         mma_bf16(z, a0, a1, a2, a3, __ldg(yb + t), __ldg(yb + t + 4));
       }
     }
-    // epilogue: lane holds rows (g, g+8), columns 2t, 2t+1 of the n-tile;
-    // the two columns move as one 16-byte access when the row allows it
-    const int64_t jj = j0 + 8 * nt + 2 * t;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t r = h ? r1 : r0;
       if (r >= da) continue;
       const float2 fa = h ? f1 : f0;
-      float2* p = vec + r * db + jj;
-      const bool pair = jj + 1 < db && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0);
-      float2 v[2];
-      if (pair) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = make_float2(q.x, q.y);
-        v[1] = make_float2(q.z, q.w);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) v[c] = jj + c < db ? p[c] : make_float2(0.f, 0.f);
-      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const int64_t j = jj + c;
-        if (j >= db) continue;
+        // z is a sum of at most 3N terms reduced to [-pi, pi]: bring it back
+        // to [-pi, pi] (2 pi in two parts) and take the hardware sincos,
+        // whose absolute error there is below 1e-6
+        const float zz = z[2 * h + c];
+        const float kq = rintf(zz * 0.15915494f);
+        const float rr = fmaf(kq, 1.7484555e-07f, fmaf(-kq, 6.28318548f, zz));  // 2 pi = hi - 1.75e-7
         float s, co;
-        sincosf(z[2 * h + c], &s, &co);
-        const float2 fb = ea_b[j];
-        const float2 fab = make_float2(fa.x * fb.x - fa.y * fb.y, fa.x * fb.y + fa.y * fb.x);
+        __sincosf(rr, &s, &co);
+        const float2 fab = make_float2(fa.x * fb[c].x - fa.y * fb[c].y,
+                                       fa.x * fb[c].y + fa.y * fb[c].x);
         const float2 f = make_float2(fab.x * co - fab.y * s, fab.x * s + fab.y * co);
-        v[c] = make_float2(f.x * v[c].x - f.y * v[c].y, f.x * v[c].y + f.y * v[c].x);
+        v[h][c] = make_float2(f.x * v[h][c].x - f.y * v[h][c].y,
+                              f.x * v[h][c].y + f.y * v[h][c].x);
       }
-      if (pair) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      float2* p = vec + r * db + jj;
+      if (pair[h]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[h][0].x, v[h][0].y, v[h][1].x, v[h][1].y);
       } else {
 #pragma unroll
         for (int c = 0; c < 2; ++c)
-          if (jj + c < db) p[c] = v[c];
+          if (jj + c < db) p[c] = v[h][c];
       }
     }
   }

@@ -18,9 +18,9 @@ constexpr int kRThreads = 256;
 // Rows: V_i[q] = sum_j W_ij occ_b(j)_q and r_i = sum_j W_ij; then
 // dJ_ab[p][q] += occ_a(i)_p V_i[q] and dJ_aa[p][q] += 1/2 r_i occ_a(i)_p occ_a(i)_q,
 // accumulated per CTA in shared memory and flushed once.
-// Per-thread partial sums run in the precision of W (FP32 for complex64
-// states, where FP64 arithmetic would be 1/64-rate); the block reduction and
-// the accumulators are FP64.
+// Per-thread partial sums and the warp sums run in the precision of W (FP32
+// for complex64 states, where FP64 arithmetic would be 1/64-rate); the block
+// reduction and the accumulators are FP64.
 template <typename R, int NQ>
 __global__ void __launch_bounds__(kRThreads)
     k_dc_rows(const R* W, int64_t da, int64_t db, const uint32_t* ma, const uint32_t* mb,
@@ -36,27 +36,36 @@ __global__ void __launch_bounds__(kRThreads)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) pacc[q] = 0;
     const R* row = W + i * db;
-    for (int64_t j = threadIdx.x; j < db; j += kRThreads) {
-      R w = row[j];
-      uint32_t m = __ldg(mb + j);
-      pr += w;
+    // eight independent loads in flight per thread before the sums
+    constexpr int U = 8;
+    for (int64_t j0 = threadIdx.x; j0 < db; j0 += U * kRThreads) {
+      R w[U];
+      uint32_t m[U];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) pacc[q] += ((m >> q) & 1u) ? w : (R)0;
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + (int64_t)u * kRThreads;
+        w[u] = j < db ? row[j] : (R)0;
+        m[u] = j < db ? __ldg(mb + j) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        pr += w[u];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) pacc[q] += ((m[u] >> q) & 1u) ? w[u] : (R)0;
+      }
     }
-    double acc[NQ];
-    double r = (double)pr;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = (double)pacc[q];
+    // warp sums in the precision of W (the FP64 shuffles of 17 values per
+    // row would cost more than reading the row on GB300), FP64 from here on
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
+      pr += __shfl_xor_sync(0xFFFFFFFFu, pr, off);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[q] += __shfl_xor_sync(0xFFFFFFFFu, acc[q], off);
+      for (int q = 0; q < NQ; ++q) pacc[q] += __shfl_xor_sync(0xFFFFFFFFu, pacc[q], off);
     }
     if (lane == 0) {
-      red[wid][NQ] = r;
+      red[wid][NQ] = (double)pr;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) red[wid][q] = acc[q];
+      for (int q = 0; q < NQ; ++q) red[wid][q] = (double)pacc[q];
     }
     __syncthreads();
     if (threadIdx.x < norb + 1) {
@@ -120,7 +129,7 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
   ProfScope ps("dc_grad", st, 3);
   const int norb = sa->norb;
   const int sms = ctx->prop.multiProcessorCount;
-  unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 2 * sms);
+  unsigned grid = (unsigned)std::min<int64_t>(sa->dim, 4 * sms);
   if (dtype == FS_C64) {
     if (norb <= 16)
       k_dc_rows<float, 16><<<grid, kRThreads, 0, st>>>((const float*)W, sa->dim, sb->dim,
@@ -150,20 +159,26 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
   FS_CUDA(cudaGetLastError());
 }
 
-// out[c][r] = in[r][c] for a rows x cols matrix of complex elements: 32 x 32
+// out[c][r] = in[r][c] for a rows x cols matrix of complex elements: square
 // tiles through shared memory, so reads and writes are both row-contiguous.
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(256)
     k_transpose(const T* __restrict__ in, T* __restrict__ out, int64_t rows, int64_t cols) {
-  __shared__ T tile[32][33];
-  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int k = ty; k < 32; k += 8) {
+  // TILE x TILE tile; 256 threads as (256 / TILE) rows of TILE lanes, so a
+  // warp reads (and writes) 32 consecutive elements of one row, and every
+  // thread keeps TILE * TILE / 256 independent loads in flight
+  constexpr int RS = 256 / TILE;
+  __shared__ T tile[TILE][TILE + 1];
+  const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
+  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
+#pragma unroll
+  for (int k = ty; k < TILE; k += RS) {
     const int64_t r = r0 + k, c = c0 + tx;
     if (r < rows && c < cols) tile[k][tx] = in[r * cols + c];
   }
   __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
+#pragma unroll
+  for (int k = ty; k < TILE; k += RS) {
     const int64_t c = c0 + k, r = r0 + tx;
     if (c < cols && r < rows) out[c * rows + r] = tile[tx][k];
   }
@@ -172,12 +187,16 @@ __global__ void __launch_bounds__(256)
 void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
                       cudaStream_t st) {
   ProfScope ps("transpose", st);
-  FS_REQUIRE((rows + 31) / 32 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  if (dtype == FS_C64)
-    k_transpose<float2><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, rows, cols);
-  else
-    k_transpose<double2><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, rows, cols);
+  if (dtype == FS_C64) {  // 64 x 64 tiles (33 KB of shared memory)
+    FS_REQUIRE((rows + 63) / 64 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
+    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
+    k_transpose<float2, 64><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, rows, cols);
+  } else {  // 32 x 32 tiles of 16-byte elements (17 KB)
+    FS_REQUIRE((rows + 31) / 32 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    k_transpose<double2, 32><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, rows,
+                                                   cols);
+  }
   FS_CUDA(cudaGetLastError());
 }
 
