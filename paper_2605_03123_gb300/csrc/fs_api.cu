@@ -140,6 +140,79 @@ static void rotate(Ctx* ctx, Space* sa, Space* sb, void* v0, void* v1, int nst, 
   launch_sweep(ctx, sa, sb, 1, v0, v1, nst, dtype, pb, phb, st);
 }
 
+// The same rotation (and fused diagonal-Coulomb evolution) with every sweep a
+// row sweep: the state alternates between vec (row-major, alpha strings on
+// rows) and tv = vec^T (beta strings on rows).  From vec (trans false): the
+// beta sweep on rows of vec, one transpose, then the alpha sweep on rows of
+// tv with the evolution in its epilogue; from tv the other way round.  The
+// two spin parts commute, so the order is free; each rotation costs one
+// transpose instead of a column sweep.  `trans` is flipped.
+static void rotate_alternating(Ctx* ctx, Space* sa, Space* sb, void* vec, void* tv, bool& trans,
+                               int dtype, const RotProgram& pa, const RotProgram& pb,
+                               const Fused* dc, cudaStream_t st) {
+  const int n = sa->norb;
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  void* ea_a = scratch(ctx, "ea_a", sa->dim * csz);
+  void* ea_b = scratch(ctx, "ea_b", sb->dim * csz);
+  void* eo_a = scratch(ctx, "alt_eo_a", sa->dim * csz);
+  void* eo_b = scratch(ctx, "alt_eo_b", sb->dim * csz);
+  const double* Jbb = dc ? (dc->J_bb ? dc->J_bb : dc->J_aa) : nullptr;
+  if (!trans) {
+    launch_string_phase(sb, ea_b, dtype, phase_of(&pb, nullptr, 0, nullptr, n), st);
+    PhaseDev p1;
+    p1.ea_b = ea_b;
+    launch_sweep(ctx, sa, sb, 1, vec, nullptr, 1, dtype, pb, p1, st);
+    launch_transpose(vec, tv, sa->dim, sb->dim, dtype, st);
+    // alpha on rows of tv: spaces swapped, this spin (alpha) in the b slot
+    PhaseDev p2;
+    if (dc) {
+      launch_string_phase(sa, ea_a, dtype, phase_of(&pa, dc->J_aa, dc->t, nullptr, n), st);
+      launch_string_phase(sb, eo_b, dtype, phase_of(nullptr, Jbb, dc->t, nullptr, n), st);
+      p2.ea_a = eo_b;
+      p2.has_x = 1;
+      for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) p2.X.v[q * n + p] = -dc->t * dc->J_ab[p * n + q];
+    } else {
+      launch_string_phase(sa, ea_a, dtype, phase_of(&pa, nullptr, 0, nullptr, n), st);
+    }
+    p2.ea_b = ea_a;
+    launch_sweep(ctx, sb, sa, 1, tv, nullptr, 1, dtype, pa, p2, st);
+    trans = true;
+  } else {
+    launch_string_phase(sa, ea_a, dtype, phase_of(&pa, nullptr, 0, nullptr, n), st);
+    PhaseDev p1;
+    p1.ea_b = ea_a;
+    launch_sweep(ctx, sb, sa, 1, tv, nullptr, 1, dtype, pa, p1, st);
+    launch_transpose(tv, vec, sb->dim, sa->dim, dtype, st);
+    PhaseDev p2;
+    if (dc) {
+      launch_string_phase(sb, ea_b, dtype, phase_of(&pb, Jbb, dc->t, nullptr, n), st);
+      launch_string_phase(sa, eo_a, dtype, phase_of(nullptr, dc->J_aa, dc->t, nullptr, n), st);
+      p2.ea_a = eo_a;
+      p2.has_x = 1;
+      p2.X = real_mat(dc->J_ab, n, -dc->t);
+    } else {
+      launch_string_phase(sb, ea_b, dtype, phase_of(&pb, nullptr, 0, nullptr, n), st);
+    }
+    p2.ea_b = ea_b;
+    launch_sweep(ctx, sa, sb, 1, vec, nullptr, 1, dtype, pb, p2, st);
+    trans = false;
+  }
+}
+
+// Whether the LUCJ passes alternate layouts: states larger than L2 (column
+// sweeps are strided there) when `extra` more states fit in device memory.
+static bool alternate_layouts(Ctx* ctx, Space* sa, Space* sb, int dtype, int extra,
+                              const char* const* names) {
+  const size_t S = (size_t)sa->dim * sb->dim * (dtype == FS_C64 ? 8 : 16);
+  if (S <= (size_t)ctx->prop.l2CacheSize) return false;
+  bool have = true;
+  for (int k = 0; k < extra; ++k) have = have && ctx->scratch[names[k]].bytes >= S;
+  if (have) return true;
+  size_t fr = 0, tot = 0;
+  return cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > extra * S + (1ull << 30);
+}
+
 // Standalone diagonal phase pass (number-operator sum and/or diagonal Coulomb).
 static void phase_pass(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
                        const StrPhase& fa, const StrPhase& fb, const double* J_ab,
@@ -616,18 +689,27 @@ int fs_lucj_forward(fs_ctx* ctx, const fs_lucj* op, void* vec, int dtype, void* 
                  phase_of(nullptr, op->J_aa, 1.0, nullptr, n), op->J_ab, -1.0, st);
       k0 = 1;
     }
+    static const char* const kFwdT[] = {"vjp_tpsi"};
+    const bool alt = k0 <= R && alternate_layouts(ctx, sa, sb, dtype, 1, kFwdT);
+    void* tv = nullptr;
+    if (alt) {
+      const size_t S = (size_t)sa->dim * sb->dim * (dtype == FS_C64 ? 8 : 16);
+      tv = scratch(ctx, "vjp_tpsi", S);
+    }
+    bool trans = false;
     for (int k = k0; k <= R; ++k) {
       RotProgram p = decompose_adjacent(n, Rs[k].data());
-      if (k < R) {
-        Fused dc;
-        dc.J_aa = op->J_aa + k * nn;
-        dc.J_ab = op->J_ab + k * nn;
-        dc.t = 1.0;
-        rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, &dc, st);
-      } else {
-        rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, nullptr, st);
-      }
+      Fused dc;
+      dc.J_aa = op->J_aa + k * nn;
+      dc.J_ab = op->J_ab + k * nn;
+      dc.t = 1.0;
+      const Fused* f = k < R ? &dc : nullptr;
+      if (alt)
+        rotate_alternating(ctx, sa, sb, vec, tv, trans, dtype, p, p, f, st);
+      else
+        rotate(ctx, sa, sb, vec, nullptr, 1, dtype, p, p, f, st);
     }
+    if (trans) launch_transpose(tv, vec, sb->dim, sa->dim, dtype, st);
   });
 }
 
@@ -1019,33 +1101,61 @@ static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int
   void* e2_a = scratch(ctx, "ea2_a", sa->dim * csz);
   void* e2_b = scratch(ctx, "ea2_b", sb->dim * csz);
   std::vector<zd> adj(nn);
+  // With transposed copies the layers alternate: from (vec, cot) the beta
+  // undo runs on rows of the states, then both are transposed and the alpha
+  // undo runs on rows of the copies, carrying W and D_{m-1}^dag; the next
+  // layer starts from the copies with the alpha undo, transposes back, and
+  // the beta undo carries W and D^dag.  The spin parts of a rotation commute
+  // and T^alpha (T^beta) is unchanged by the beta (alpha) rotation, so the
+  // order is free; each layer costs two transposes.
+  bool trans = false;
   for (int m = R; m >= 0; --m) {
     mat_adjoint(n, Rs[m].data(), adj.data());
     RotProgram inv = decompose_adjacent(n, adj.data());
     double* Tm = Tacc + (size_t)m * nn * 2;
-    // beta: undo, T^beta
+    const double* Ja = m >= 1 ? op->J_aa + (size_t)(m - 1) * nn : nullptr;
+    const double* Jab = m >= 1 ? op->J_ab + (size_t)(m - 1) * nn : nullptr;
+    if (m >= 1) {
+      launch_string_phase(sa, e2_a, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
+      launch_string_phase(sb, e2_b, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
+    }
     launch_string_phase(sb, ea_b, dtype, phase_of(&inv, nullptr, 0, nullptr, n), st);
+    launch_string_phase(sa, ea_a, dtype, phase_of(&inv, nullptr, 0, nullptr, n), st);
+    if (alpha_t && trans) {
+      // alpha: undo on rows of the copies, T^alpha
+      PhaseDev q1;
+      q1.ea_b = ea_a;
+      RevArgs t1;
+      t1.T = Tm;
+      launch_sweep(ctx, sb, sa, 1, tpsi, tg, 2, dtype, inv, q1, st, &t1);
+      launch_transpose(tpsi, vec, sb->dim, sa->dim, dtype, st);
+      launch_transpose(tg, cot, sb->dim, sa->dim, dtype, st);
+      // beta: undo, T^beta, W and D_{m-1}^dag
+      PhaseDev p2;
+      p2.ea_b = ea_b;
+      RevArgs r2;
+      r2.T = Tm;
+      if (m >= 1) {
+        r2.ea2_a = e2_a;
+        r2.ea2_b = e2_b;
+        r2.W = Wb;
+        p2.has_x = 1;
+        p2.X = real_mat(Jab, n, 1.0);
+      }
+      launch_sweep(ctx, sa, sb, 1, vec, cot, 2, dtype, inv, p2, st, &r2);
+      if (m >= 1)
+        launch_dc_grad(ctx, sa, sb, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
+                       dJab_d + (size_t)(m - 1) * nn, st);
+      trans = false;
+      continue;
+    }
+    // beta: undo, T^beta
     PhaseDev p1;
     p1.ea_b = ea_b;
     RevArgs r1;
     r1.T = Tm;
     launch_sweep(ctx, sa, sb, 1, vec, cot, 2, dtype, inv, p1, st, &r1);
     // alpha: undo, T^alpha, W and D_{m-1}^dag
-    launch_string_phase(sa, ea_a, dtype, phase_of(&inv, nullptr, 0, nullptr, n), st);
-    PhaseDev p2;
-    p2.ea_a = ea_a;
-    RevArgs r2;
-    r2.T = Tm;
-    if (m >= 1) {
-      const double* Ja = op->J_aa + (size_t)(m - 1) * nn;
-      launch_string_phase(sa, e2_a, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
-      launch_string_phase(sb, e2_b, dtype, phase_of(nullptr, Ja, -1.0, nullptr, n), st);
-      r2.ea2_a = e2_a;
-      r2.ea2_b = e2_b;
-      r2.W = Wb;
-      p2.has_x = 1;
-      p2.X = real_mat(op->J_ab + (size_t)(m - 1) * nn, n, 1.0);
-    }
     if (alpha_t) {
       // the same sweep as a row sweep of the transposed states: this spin
       // (alpha) along rows of length dim_a, the cross angles transposed
@@ -1060,22 +1170,35 @@ static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int
         t2.ea2_a = e2_b;
         t2.W = Wb;
         q2.has_x = 1;
-        const double* Jab = op->J_ab + (size_t)(m - 1) * nn;
         for (int p = 0; p < n; ++p)
           for (int q = 0; q < n; ++q) q2.X.v[q * n + p] = Jab[p * n + q];
       }
       launch_sweep(ctx, sb, sa, 1, tpsi, tg, 2, dtype, inv, q2, st, &t2);
-      launch_transpose(tpsi, vec, sb->dim, sa->dim, dtype, st);
-      launch_transpose(tg, cot, sb->dim, sa->dim, dtype, st);
       if (m >= 1)
         launch_dc_grad(ctx, sb, sa, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
                        dJabT_d + (size_t)(m - 1) * nn, st);
+      trans = true;
     } else {
+      PhaseDev p2;
+      p2.ea_a = ea_a;
+      RevArgs r2;
+      r2.T = Tm;
+      if (m >= 1) {
+        r2.ea2_a = e2_a;
+        r2.ea2_b = e2_b;
+        r2.W = Wb;
+        p2.has_x = 1;
+        p2.X = real_mat(Jab, n, 1.0);
+      }
       launch_sweep(ctx, sa, sb, 0, vec, cot, 2, dtype, inv, p2, st, &r2);
       if (m >= 1)
         launch_dc_grad(ctx, sa, sb, Wb, dtype, dJaa_d + (size_t)(m - 1) * nn,
                        dJab_d + (size_t)(m - 1) * nn, st);
     }
+  }
+  if (trans) {
+    launch_transpose(tpsi, vec, sb->dim, sa->dim, dtype, st);
+    launch_transpose(tg, cot, sb->dim, sa->dim, dtype, st);
   }
   std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn), dJT;
   FS_CUDA(cudaMemcpyAsync(Th.data(), Tacc, Th.size() * 8, cudaMemcpyDeviceToHost, st));

@@ -219,6 +219,27 @@ def test_lucj_vjp_full_size_properties(lib, dt):
     assert np.all(np.isfinite(dK)) and np.all(np.isfinite(dJa)) and np.all(np.isfinite(dJb))
 
 
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_lucj_forward_full_size_matches_gate_composition(lib, dt):
+    """N=16 (8,8), 2 layers: the LUCJ forward pass (merged rotations, the
+    diagonal-Coulomb gates fused into sweeps, the layouts alternating between
+    the state and its transpose) equals, element by element, the literal
+    composition U(U_k) D(J_k) U(U_k)^dag of the separate gate calls."""
+    from scipy.linalg import expm
+    w = inputs.lucj_layers(16, (8, 8), 2, 0.5, 0.3, 2000 + 9, with_cot=False)
+    norb, nelec = 16, (8, 8)
+    x = dev(w["vec"], dt)
+    lib.lucj_forward_(x, w["K"], w["J_aa"], w["J_ab"], norb, nelec)
+    y = dev(w["vec"], dt)
+    for K, Ja, Jb in zip(w["K"], w["J_aa"], w["J_ab"]):
+        U = expm(K)
+        lib.apply_orbital_rotation_(y, U.conj().T, norb, nelec)
+        lib.apply_diag_coulomb_evolution_(y, Ja, Jb, 1.0, norb, nelec)
+        lib.apply_orbital_rotation_(y, U, norb, nelec)
+    err = float((x.to(torch.complex128) - y.to(torch.complex128)).abs().max())
+    assert err < TOL[dt], err
+
+
 def test_autograd_function_matches_oracle(lib):
     from paper_2605_03123_gb300.autograd import lucj
     norb, nelec, n_reps = 6, (3, 2), 2
