@@ -29,7 +29,11 @@
  * 2*N*N doubles (interleaved re, im); a real N x N matrix is N*N doubles.
  *
  * Asynchrony: calls enqueue work on `stream` and return; host inputs are
- * copied before the call returns, so they may be reused at once.  Calls
+ * copied before the call returns, so they may be reused at once.  Calls on
+ * one context share its scratch buffers (host calls on a context are
+ * serialised by a lock, GPU work is not): issue them on one stream, or
+ * order their streams, since calls of one context that overlap on the GPU
+ * race on that scratch.  Separate contexts have separate scratch.  Calls
  * that return host outputs (fs_lucj_vjp gradients, fs_string_table,
  * fs_excitation_table) synchronize the stream before returning.
  *
