@@ -81,3 +81,33 @@ def test_hermitian_tensors_give_a_hermitian_operator():
     lhs = np.vdot(u, oracle.apply_molecular_hamiltonian(w, h1, h2, N, nelec))
     rhs = np.vdot(oracle.apply_molecular_hamiltonian(u, h1, h2, N, nelec), w)
     assert abs(lhs - rhs) < 1e-11
+
+
+def test_jordan_wigner_pin_catches_planted_mistakes(fock3, monkeypatch):
+    """Mistakes planted in the oracle's operator strings fail the dense
+    Jordan-Wigner pin: the fermionic signs dropped, and the two annihilators
+    of the two-body term applied in the wrong order."""
+    import oracle.operator as oo
+    fs, N, nelec = fock3, 3, (2, 2)
+    g = inputs.rng(1190)
+    h1, h2 = _tensors(N, g)
+    v = inputs.random_state(N, nelec, g)
+    ref = fs.extract(_dense(fs, h1, h2, 0.0) @ fs.embed(v, nelec), nelec)
+    orig = oo._spin_map
+
+    def no_signs(norb, nocc, ops):
+        src, dst, sgn = orig(norb, nocc, ops)
+        return src, dst, np.abs(sgn)
+
+    def swapped(norb, nocc, ops):
+        if len(ops) == 4:
+            ops = [ops[0], ops[1], ops[3], ops[2]]
+        return orig(norb, nocc, ops)
+
+    for bad in (no_signs, swapped):
+        monkeypatch.setattr(oo, "_spin_map", bad)
+        got = oo.apply_molecular_hamiltonian(v, h1, h2, N, nelec)
+        assert np.max(np.abs(got - ref)) > 1e-3
+        monkeypatch.undo()
+    got = oo.apply_molecular_hamiltonian(v, h1, h2, N, nelec)
+    assert np.max(np.abs(got - ref)) < 1e-11
