@@ -16,8 +16,10 @@ or a Slater determinant.  Each function is pinned by tests that do not reuse it:
 Jordan-Wigner construction with matrix exponentials (`bruteforce`), the
 Slater-determinant closed form (§2.4), the group-homomorphism identities of
 §2.3, the gate equivalences listed after Table 1, the state sizes printed in
-§1, §5.2 and §6.1, finite differences for the gradient, and the convergence
-order of the product formulas against exact evolution.
+§1, §5.2 and §6.1, finite differences for the gradient, the convergence
+order of the product formulas against exact evolution, and for the samplers
+the chain rule summed over pick orders against |det U[I, occ]|^2 and sample
+frequencies against the exact distributions.
 """
 
 from .strings import strings, address_map, occupations, excite
