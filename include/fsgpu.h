@@ -61,7 +61,7 @@ typedef enum {
   FS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
   FS_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
   FS_ERR_BOUNDS = -6,      /* a device-side index check failed */
-  FS_ERR_UNSUPPORTED = -7  /* valid request outside what this build supports */
+  FS_ERR_UNSUPPORTED = -7  /* valid request outside what the library supports */
 } fs_status;
 
 typedef enum { FS_C64 = 0, FS_C128 = 1 } fs_dtype;
