@@ -156,14 +156,15 @@ int fs_apply_diag_coulomb_evolution(fs_ctx *ctx, void *vec, int dtype,
  * allocating library routine): its scratch (string masks and per-string
  * phase factors, 640 KiB) is one static device array that every GPU which
  * loads the library holds until the process exits.  The caller still owns
- * `vec`.  Arguments and results are those of
+ * `vec`, which must be device memory of the current device (else
+ * FS_ERR_ARG).  Arguments and results are those of
  * fs_apply_diag_coulomb_evolution; each spin may have at most 16384 strings
  * (C(norb, n) <= 16384), larger sectors return FS_ERR_UNSUPPORTED before any
  * work is enqueued.
  *
- * The first call on a device looks up the array's device address and
- * uploads a small constant table with that device current; make that first
- * call before any stream capture.  All calls share the one array and
+ * The first call on a device looks up the array's device address with that
+ * device current and loads every kernel the call launches, in both
+ * precisions; make that first call before any stream capture.  All calls share the one array and
  * overwrite all of it that they read, so nothing carries over between calls;
  * calls that overlap on the GPU (on different streams, or from different
  * host threads without ordering) race on it. */

@@ -25,6 +25,7 @@ frequencies against the exact distributions.
 from .strings import strings, address_map, occupations, excite
 from .gates import (dims, hartree_fock, apply_num_op_sum_evolution,
                     apply_diag_coulomb_evolution, diag_coulomb_angle,
+                    diag_coulomb_angle_entry, rotated_string,
                     minor_matrix, minor_matrix_row, rotated_amplitude,
                     apply_orbital_rotation,
                     apply_orbital_rotation_minors, apply_orbital_rotation_givens,

@@ -73,6 +73,33 @@ def diag_coulomb_angle(J_aa, J_ab, J_bb, t, norb, nelec):
     return -0.5 * t * (aa[:, None] + ab + bb[None, :])
 
 
+def diag_coulomb_angle_entry(J_aa, J_ab, J_bb, t, norb, nelec, i, j):
+    """theta of the single determinant with alpha address i and beta address
+    j: the same multiset sum over occupied pairs as `diag_coulomb_angle`
+    (p == q included, J_ba = J_ab^T), written out for one determinant, for
+    checks at sizes where the whole angle matrix is too large."""
+    if J_bb is None:
+        J_bb = J_aa
+    J_aa = np.asarray(J_aa, float)
+    J_ab = np.asarray(J_ab, float)
+    J_bb = np.asarray(J_bb, float)
+    ma = int(strings(norb, nelec[0])[i])
+    mb = int(strings(norb, nelec[1])[j])
+    oa = [p for p in range(norb) if (ma >> p) & 1]
+    ob = [p for p in range(norb) if (mb >> p) & 1]
+    s = 0.0
+    for p in oa:
+        for q in oa:
+            s += J_aa[p, q]
+    for p in ob:
+        for q in ob:
+            s += J_bb[p, q]
+    for p in oa:
+        for q in ob:
+            s += J_ab[p, q] + J_ab[p, q]      # (p in I_a, q in I_b) and its J_ba mirror
+    return -0.5 * t * s
+
+
 def apply_diag_coulomb_evolution(vec, J_aa, J_ab, J_bb, t, norb, nelec):
     theta = diag_coulomb_angle(J_aa, J_ab, J_bb, t, norb, nelec)
     return np.exp(1j * theta) * vec
@@ -109,6 +136,17 @@ def minor_matrix_row(U, norb, nocc, a):
     occ = np.array([[p for p in range(norb) if (int(m) >> p) & 1] for m in s])
     sub = np.asarray(U, complex)[occ[a], :]
     return np.linalg.det(np.transpose(sub[:, occ], (1, 0, 2)))
+
+
+def rotated_string(U, norb, nocc, b):
+    """Amplitudes of U(U)|I_b> for one spin over every string J: column b of
+    the minor matrix, det(U[J, I_b])."""
+    s = strings(norb, nocc)
+    if nocc == 0:
+        return np.ones(1, np.complex128)
+    occ = np.array([[p for p in range(norb) if (int(m) >> p) & 1] for m in s])
+    sub = np.asarray(U, complex)[:, occ[b]]     # all rows, the columns of I_b
+    return np.linalg.det(sub[occ, :])          # [J][rows J][columns I_b]
 
 
 def rotated_amplitude(vec, U_a, U_b, norb, nelec, i, j):

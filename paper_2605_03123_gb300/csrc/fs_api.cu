@@ -290,22 +290,6 @@ static void rotate_any(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
     rotate(ctx, sa, sb, vec, nullptr, 1, dtype, pa, pb, nullptr, st);
 }
 
-template <class F>
-static int guarded(F&& f) {
-  try {
-    f();
-    return FS_OK;
-  } catch (Fail& e) {
-    return e.code;
-  } catch (std::bad_alloc&) {
-    set_error("host allocation failed");
-    return FS_ERR_NOMEM;
-  } catch (std::exception& e) {
-    set_error(e.what());
-    return FS_ERR_ARG;
-  }
-}
-
 static void lucj_checks(Ctx* ctx, const fs_lucj* op, void* vec, int dtype) {
   FS_REQUIRE(op != nullptr, FS_ERR_ARG, "null LUCJ operator");
   check_sector(ctx, vec, dtype, op->norb, op->n_alpha, op->n_beta);

@@ -7,6 +7,8 @@
 #include <map>
 #include <tuple>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <utility>
 #include <vector>
@@ -228,6 +230,25 @@ struct Fail {
     }                                  \
   } while (0)
 
+// Runs the body of a C entry point and maps what it throws to a status
+// code: Fail carries its own code, a failed host allocation is
+// FS_ERR_NOMEM, any other standard exception FS_ERR_ARG.
+template <class F>
+static int guarded(F&& f) {
+  try {
+    f();
+    return FS_OK;
+  } catch (Fail& e) {
+    return e.code;
+  } catch (std::bad_alloc&) {
+    set_error("host allocation failed");
+    return FS_ERR_NOMEM;
+  } catch (std::exception& e) {
+    set_error(e.what());
+    return FS_ERR_ARG;
+  }
+}
+
 // ------------------------------------------------------ kernel launchers
 // Small matrices travel to the kernels by value, as kernel parameters.
 struct Mat {
@@ -417,5 +438,10 @@ void launch_minor_rotation(Ctx* ctx, const Space* sa, const Space* sb, void* vec
                            const CMat& Ua, const CMat& Ub, cudaStream_t st);
 // masks[dim] of the strings of nocc electrons in norb orbitals, into `out`.
 void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st);
+// Force the module loads of the kernels the allocation-free entry point
+// launches (k_masks; k_string_phase and k_phase in both precisions), so
+// that none of them loads lazily on a later call.
+void preload_mask_kernel();
+void preload_phase_kernels();
 
 }  // namespace fs

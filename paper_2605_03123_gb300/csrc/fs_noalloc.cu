@@ -24,12 +24,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of the array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-static unsigned char* noalloc_scratch_address() {
+// once per device (with that device current) and cached.  The same first
+// call also loads every kernel this entry point launches, so no module
+// loads lazily on a later call (for instance inside a stream capture).
+static unsigned char* noalloc_scratch_address(int dev) {
   static std::mutex m;
   static unsigned char* addr[256] = {};
-  int dev = 0;
-  FS_CUDA(cudaGetDevice(&dev));
   FS_REQUIRE(dev >= 0 && dev < 256, FS_ERR_UNSUPPORTED, "device index above 255");
   std::lock_guard<std::mutex> g(m);
   if (!addr[dev]) {
@@ -40,9 +40,28 @@ static unsigned char* noalloc_scratch_address() {
                 cudaGetErrorString(e));
       throw Fail{FS_ERR_CUDA};
     }
+    preload_mask_kernel();
+    preload_phase_kernels();
     addr[dev] = (unsigned char*)p;
   }
   return addr[dev];
+}
+
+// The state must be device memory of the current device: the kernels run
+// there, and a pointer into another GPU's memory would be dereferenced
+// across devices.  cudaPointerGetAttributes allocates nothing.
+static void require_current_device_memory(const void* vec, int dev) {
+  cudaPointerAttributes pa;
+  const cudaError_t e = cudaPointerGetAttributes(&pa, vec);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not sticky; clear it
+    set_error(std::string("the state pointer is not a CUDA pointer: ") + cudaGetErrorString(e));
+    throw Fail{FS_ERR_ARG};
+  }
+  FS_REQUIRE(pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged, FS_ERR_ARG,
+             "the state must be device memory");
+  FS_REQUIRE(pa.device == dev, FS_ERR_ARG,
+             "the state lives on another device than the current one");
 }
 
 static int64_t dim_of(int norb, int nocc) { return (int64_t)binom_host(norb, nocc); }
@@ -55,7 +74,7 @@ extern "C" int fs_apply_diag_coulomb_evolution_noalloc(void* vec, int dtype, con
                                                        const double* J_ab, const double* J_bb,
                                                        double t, int norb, int n_alpha,
                                                        int n_beta, void* stream) {
-  try {
+  return guarded([&] {
     FS_REQUIRE(dtype == FS_C64 || dtype == FS_C128, FS_ERR_ARG,
                "dtype must be FS_C64 or FS_C128");
     FS_REQUIRE(norb >= 1 && norb <= kMaxNorb, FS_ERR_ARG, "norb must be in [1, 32]");
@@ -69,9 +88,12 @@ extern "C" int fs_apply_diag_coulomb_evolution_noalloc(void* vec, int dtype, con
     FS_REQUIRE(da <= kNoAllocMaxDim && db <= kNoAllocMaxDim, FS_ERR_UNSUPPORTED,
                "fs_apply_diag_coulomb_evolution_noalloc accepts at most 16384 strings per "
                "spin; use fs_apply_diag_coulomb_evolution for larger sectors");
+    int dev = 0;
+    FS_CUDA(cudaGetDevice(&dev));
+    require_current_device_memory(vec, dev);
     current_ctx() = nullptr;  // no tracing on this path
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned char* base = noalloc_scratch_address();
+    unsigned char* base = noalloc_scratch_address(dev);
     Space sa, sb;
     sa.norb = sb.norb = norb;
     sa.nocc = n_alpha;
@@ -100,11 +122,5 @@ extern "C" int fs_apply_diag_coulomb_evolution_noalloc(void* vec, int dtype, con
     ph.has_x = 1;
     for (int k = 0; k < norb * norb; ++k) ph.X.v[k] = -t * J_ab[k];
     launch_phase(&sa, &sb, vec, dtype, ph, st);
-    return FS_OK;
-  } catch (Fail& e) {
-    return e.code;
-  } catch (std::exception& e) {
-    set_error(e.what());
-    return FS_ERR_ARG;
-  }
+  });
 }

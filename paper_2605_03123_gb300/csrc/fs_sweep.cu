@@ -1310,6 +1310,14 @@ __global__ void k_string_phase(cx_t<R>* out, const uint32_t* masks, int64_t dim,
   out[e] = mk<R>((R)(re * c - im * s), (R)(re * s + im * c));
 }
 
+void preload_phase_kernels() {
+  cudaFuncAttributes fa;
+  FS_CUDA(cudaFuncGetAttributes(&fa, k_string_phase<float>));
+  FS_CUDA(cudaFuncGetAttributes(&fa, k_string_phase<double>));
+  FS_CUDA(cudaFuncGetAttributes(&fa, k_phase<float>));
+  FS_CUDA(cudaFuncGetAttributes(&fa, k_phase<double>));
+}
+
 void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& f,
                          cudaStream_t st) {
   ProfScope ps("string_phase", st);

@@ -258,6 +258,11 @@ void free_space(Space* s) {
   delete s;
 }
 
+void preload_mask_kernel() {
+  cudaFuncAttributes fa;
+  FS_CUDA(cudaFuncGetAttributes(&fa, k_masks));
+}
+
 void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st) {
   upload_binomials();
   int64_t dim = choose(norb, nocc);

@@ -253,15 +253,19 @@ def apply_diag_coulomb_evolution(vec, J_aa, J_ab, t, norb, nelec, J_bb=None, ctx
 def apply_diag_coulomb_evolution_noalloc_(vec, J_aa, J_ab, t, norb, nelec, J_bb=None):
     """In-place diagonal-Coulomb evolution that allocates no device memory
     (for callers that must not allocate; at most 16384 strings per spin).
-    Uses the current device and stream; needs no context."""
+    Runs on the state's own device and that device's current stream; needs
+    no context."""
     _check_state(vec, norb, nelec)
     a = _f64(J_aa, (norb, norb))
     b = _f64(J_ab, (norb, norb))
     c = None if J_bb is None else _f64(J_bb, (norb, norb))
-    _check("fs_apply_diag_coulomb_evolution_noalloc",
-           load_library().fs_apply_diag_coulomb_evolution_noalloc(
-               _P(vec.data_ptr()), _dtype_code(vec), _ptr(a), _ptr(b), _ptr(c), float(t),
-               norb, nelec[0], nelec[1], _stream_ptr()))
+    import torch
+    with torch.cuda.device(vec.device):
+        stream = torch.cuda.current_stream(vec.device).cuda_stream
+        _check("fs_apply_diag_coulomb_evolution_noalloc",
+               load_library().fs_apply_diag_coulomb_evolution_noalloc(
+                   _P(vec.data_ptr()), _dtype_code(vec), _ptr(a), _ptr(b), _ptr(c),
+                   float(t), norb, nelec[0], nelec[1], _P(stream)))
     return vec
 
 

@@ -78,6 +78,12 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
+def _elementwise(a, b):
+    """max |a - b| over the entries, relative to max |b|: a wrong small entry
+    (an off-pattern coupling, say) cannot hide under the norm of the rest."""
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
 def _small_case(norb, nelec, n_reps, seed, from_hf):
     g = inputs.rng(seed)
     K = np.array([inputs.random_antihermitian(norb, 0.5, g) for _ in range(n_reps)])
@@ -101,6 +107,9 @@ def test_lucj_vjp_small_against_oracle(lib, dt, norb, nelec, n_reps, from_hf):
     dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec, from_hf=from_hf)
     tol = 1e-11 if dt == "c128" else 2e-4
     assert _rel(dK, rK) < tol and _rel(dJa, rJa) < tol and _rel(dJb, rJb) < tol
+    tel = 1e-6 if dt == "c128" else 1e-3
+    for a, b in ((dK, rK), (dJa, rJa), (dJb, rJb)):
+        assert _elementwise(a, b) < tel
     v_in = oracle.hartree_fock(norb, nelec) if from_hf else v
     assert np.max(np.abs(host(x) - v_in)) < TOL[dt]            # uncomputed input
     if not from_hf:
@@ -127,6 +136,7 @@ def test_lucj_vjp_n12_against_oracle(lib, dt, lucj_small_vjp_ref):
     tol = 1e-6 if dt == "c128" else 1e-3
     for a, b in ((dK, rK), (dJa, rJa), (dJb, rJb)):
         assert _rel(a, b) < tol
+        assert _elementwise(a, b) < tol
     assert np.max(np.abs(host(x) - oracle.hartree_fock(norb, nelec))) < TOL[dt]
 
 
@@ -270,6 +280,8 @@ def test_lucj_vjp_cluster_path_against_oracle(lib):
     cg = dev(c, "c128")
     dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec)
     assert _rel(dK, rK) < 1e-10 and _rel(dJa, rJa) < 1e-10 and _rel(dJb, rJb) < 1e-10
+    for a, b in ((dK, rK), (dJa, rJa), (dJb, rJb)):
+        assert _elementwise(a, b) < 1e-6
     assert np.max(np.abs(host(cg) - rv)) < 1e-12
     assert np.max(np.abs(host(x) - v)) < 1e-12
 
@@ -297,6 +309,9 @@ def test_lucj_blocked_clusters_against_oracle(lib, dt, n18_cluster_case):
     dK, dJa, dJb = lib.lucj_vjp_(x, cg, K, Jaa, Jab, norb, nelec)
     tg = 1e-10 if dt == "c128" else 2e-4
     assert _rel(dK, rK) < tg and _rel(dJa, rJa) < tg and _rel(dJb, rJb) < tg
+    te = 1e-6 if dt == "c128" else 1e-3
+    for a, b in ((dK, rK), (dJa, rJa), (dJb, rJb)):
+        assert _elementwise(a, b) < te
     assert np.max(np.abs(host(cg) - rv)) < TOL[dt]
     assert np.max(np.abs(host(x) - v)) < TOL[dt]
 

@@ -302,6 +302,188 @@ def test_lucj_gradient_by_central_differences(from_hf):
                 assert abs(fd - an) < 1e-7
 
 
+# ---------------------------------------- single rows and single amplitudes
+def _minor_sectors():
+    return [(5, 0), (5, 1), (5, 2), (6, 3), (7, 4), (8, 1), (8, 4), (8, 7), (8, 8)]
+
+
+@pytest.mark.parametrize("norb,nocc", _minor_sectors())
+def test_minor_matrix_row_is_a_row_of_the_minor_matrix(norb, nocc):
+    """Every row of minor_matrix_row equals the corresponding row of the full
+    minor matrix, itself pinned to dense Jordan-Wigner evolution above."""
+    g = _rs(4100 + 17 * norb + nocc)
+    U = inputs.haar_unitary(norb, g)
+    M = oracle.minor_matrix(U, norb, nocc)
+    for a in range(M.shape[0]):
+        row = oracle.minor_matrix_row(U, norb, nocc, a)
+        assert np.max(np.abs(row - M[a])) < 1e-13, (norb, nocc, a)
+
+
+def test_minor_matrix_row_closed_forms():
+    """One electron: strings are single orbitals in order, so row a of the
+    minor matrix is row a of U (c' = U c).  A full shell has one string
+    whose amplitude is multiplied by det U.  No electrons: the vacuum is
+    left unchanged."""
+    g = _rs(4200)
+    for norb in (1, 3, 8):
+        U = inputs.haar_unitary(norb, g)
+        for a in range(norb):
+            assert np.max(np.abs(oracle.minor_matrix_row(U, norb, 1, a) - U[a])) < 1e-15
+        full = oracle.minor_matrix_row(U, norb, norb, 0)
+        assert full.shape == (1,) and abs(full[0] - np.linalg.det(U)) < 1e-13
+        assert np.array_equal(oracle.minor_matrix_row(U, norb, 0, 0), np.ones(1))
+
+
+def test_rotated_amplitude_matches_jordan_wigner(fock3, fock4):
+    """Single amplitudes of the rotated state against dense Jordan-Wigner
+    evolution with expm (§2.3), every sector at N = 3 and 4."""
+    for fs in (fock3, fock4):
+        norb = fs.norb
+        for k, nelec in enumerate(_sectors(norb)):
+            g = _rs(4300 + 11 * k + norb)
+            Ua = inputs.haar_unitary(norb, g)
+            Ub = inputs.haar_unitary(norb, g)
+            v = inputs.random_state(norb, nelec, g)
+            ref = bf.orbital_rotation(fs, Ua, Ub, v, nelec)
+            for i in range(ref.shape[0]):
+                for j in range(ref.shape[1]):
+                    got = oracle.rotated_amplitude(v, Ua, Ub, norb, nelec, i, j)
+                    assert abs(got - ref[i, j]) < 1e-12, (nelec, i, j)
+
+
+def test_rotated_amplitude_matches_jordan_wigner_n5():
+    fs = bf.FockSpace(5)
+    for nelec in [(2, 3), (4, 1)]:
+        g = _rs(4400 + 7 * nelec[0] + nelec[1])
+        U = inputs.haar_unitary(5, g)
+        v = inputs.random_state(5, nelec, g)
+        ref = bf.orbital_rotation(fs, U, None, v, nelec)
+        for i in range(ref.shape[0]):
+            for j in range(0, ref.shape[1], 2):
+                got = oracle.rotated_amplitude(v, U, None, 5, nelec, i, j)
+                assert abs(got - ref[i, j]) < 1e-12
+
+
+@pytest.mark.parametrize("norb,nelec", [(6, (3, 2)), (8, (4, 4)), (8, (1, 7)), (7, (0, 3))])
+def test_rotated_amplitude_matches_full_minor_rotation(norb, nelec):
+    """At N up to 8 every amplitude of the single-entry route equals the
+    whole-state minor route and the independent Givens route."""
+    g = _rs(4500 + norb + 3 * nelec[0])
+    Ua = inputs.haar_unitary(norb, g)
+    Ub = inputs.haar_unitary(norb, g)
+    v = inputs.random_state(norb, nelec, g)
+    full = oracle.apply_orbital_rotation_minors(v, Ua, Ub, norb, nelec)
+    giv = oracle.apply_orbital_rotation(v, Ua, Ub, norb, nelec, route="givens")
+    assert np.max(np.abs(full - giv)) < 1e-12
+    rows = range(full.shape[0])
+    cols = range(full.shape[1])
+    for i in rows:
+        for j in cols:
+            got = oracle.rotated_amplitude(v, Ua, Ub, norb, nelec, i, j)
+            assert abs(got - full[i, j]) < 1e-12, (i, j)
+
+
+@pytest.mark.parametrize("norb,nocc", [(4, 2), (6, 3), (7, 1), (8, 4), (5, 5)])
+def test_rotated_string_is_a_column_of_the_minor_matrix(norb, nocc):
+    g = _rs(4700 + norb * 3 + nocc)
+    U = inputs.haar_unitary(norb, g)
+    M = oracle.minor_matrix(U, norb, nocc)
+    for b in range(M.shape[1]):
+        assert np.max(np.abs(oracle.rotated_string(U, norb, nocc, b) - M[:, b])) < 1e-13
+
+
+def test_rotated_string_of_hartree_fock_is_the_slater_closed_form():
+    """b = 0 is the Hartree-Fock string: U|HF> per spin (§2.4)."""
+    g = _rs(4750)
+    U = inputs.haar_unitary(7, g)
+    ref = oracle.slater_from_hf(U, U, 7, (3, 3))
+    va = oracle.rotated_string(U, 7, 3, 0)
+    assert np.max(np.abs(np.outer(va, va) - ref)) < 1e-13
+
+
+def test_rotated_string_matches_jordan_wigner(fock4):
+    """U(U_a) x U(U_b) on one basis determinant against dense evolution."""
+    fs = fock4
+    for k, nelec in enumerate([(2, 2), (1, 3), (3, 0)]):
+        g = _rs(4800 + k)
+        Ua, Ub = inputs.haar_unitary(4, g), inputs.haar_unitary(4, g)
+        da, db = oracle.dims(4, nelec)
+        for i in range(da):
+            for j in range(db):
+                e = np.zeros((da, db), complex)
+                e[i, j] = 1
+                ref = bf.orbital_rotation(fs, Ua, Ub, e, nelec)
+                got = np.outer(oracle.rotated_string(Ua, 4, nelec[0], i),
+                               oracle.rotated_string(Ub, 4, nelec[1], j))
+                assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("norb,nelec", [(3, (2, 1)), (4, (2, 2)), (6, (3, 2)), (7, (0, 4))])
+def test_diag_coulomb_angle_entry_matches_whole_matrix(norb, nelec):
+    """The single-determinant angle against the whole angle matrix (pinned
+    to dense Jordan-Wigner evolution above) with a non-symmetric J_ab."""
+    g = _rs(4900 + norb)
+    Jaa = inputs.random_symmetric(norb, 1.0, g)
+    Jab = g.normal(0, 1, (norb, norb))
+    Jbb = inputs.random_symmetric(norb, 1.0, g)
+    for jbb in (Jbb, None):
+        th = oracle.diag_coulomb_angle(Jaa, Jab, jbb, 0.37, norb, nelec)
+        for i in range(th.shape[0]):
+            for j in range(th.shape[1]):
+                got = oracle.diag_coulomb_angle_entry(Jaa, Jab, jbb, 0.37, norb, nelec, i, j)
+                assert abs(got - th[i, j]) < 1e-12
+
+
+def test_diag_coulomb_angle_entry_matches_jordan_wigner(fock3):
+    """exp(i theta) of every determinant against dense expm of the
+    diagonal-Coulomb operator (§3.2.2)."""
+    fs = fock3
+    nelec = (2, 1)
+    g = _rs(4950)
+    Jaa = inputs.random_symmetric(3, 1.0, g)
+    Jab = g.normal(0, 1, (3, 3))
+    da, db = oracle.dims(3, nelec)
+    ones = np.ones((da, db), complex)
+    ref = bf.diag_coulomb(fs, Jaa, Jab, None, 0.8, ones, nelec)
+    for i in range(da):
+        for j in range(db):
+            th = oracle.diag_coulomb_angle_entry(Jaa, Jab, None, 0.8, 3, nelec, i, j)
+            assert abs(np.exp(1j * th) - ref[i, j]) < 1e-12
+    # planted mistakes: a dropped 1/2, or the mixed term counted once
+    th_bad = -0.8 * sum(Jaa[p, q] for p in (0, 1) for q in (0, 1))
+    assert abs(np.exp(1j * th_bad) - ref[0, 0]) > 1e-3
+
+
+def test_single_amplitude_pins_catch_planted_mistakes(fock3):
+    """A row/column mix-up or a transposed U inside the single-row minor
+    route fails the pins above."""
+    fs = fock3
+    nelec = (2, 1)
+    g = _rs(4600)
+    Ua = inputs.haar_unitary(3, g)
+    Ub = inputs.haar_unitary(3, g)
+    v = inputs.random_state(3, nelec, g)
+    ref = bf.orbital_rotation(fs, Ua, Ub, v, nelec)
+    M = oracle.minor_matrix(Ua, 3, 2)
+
+    def column_instead_of_row(U, norb, nocc, a):
+        s = oracle.strings(norb, nocc)
+        occ = np.array([[p for p in range(norb) if (int(m) >> p) & 1] for m in s])
+        sub = np.asarray(U, complex)[:, occ[a]]           # columns I_a: wrong
+        return np.linalg.det(sub[occ, :])                  # det U[I, I_a] = M[I, a]
+
+    bad_rows = [column_instead_of_row(Ua, 3, 2, a) for a in range(3)]
+    assert max(np.max(np.abs(r - M[a])) for a, r in enumerate(bad_rows)) > 1e-3
+    # a transposed U in both spins
+    worst = max(abs(oracle.rotated_amplitude(v, Ua.T, Ub.T, 3, nelec, i, j) - ref[i, j])
+                for i in range(3) for j in range(3))
+    assert worst > 1e-3
+    # the spins swapped
+    worst = max(abs(oracle.rotated_amplitude(v, Ub, Ua, 3, nelec, i, j) - ref[i, j])
+                for i in range(3) for j in range(3))
+    assert worst > 1e-3
+
+
 # ------------------------------------------------- planted mistakes (CPU)
 def test_pins_catch_planted_mistakes(monkeypatch, fock3):
     """Plant plausible mistakes in the oracle and check that a pin fails."""
