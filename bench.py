@@ -147,20 +147,23 @@ def algorithmic_bytes(kernel, S, n_layers):
     return None
 
 
+FLOPS_PER_ELEMENT_GIVENS = 10
+
+
 def algorithmic_flops(kernel, norb, nelec, amplitudes):
-    """FP32 (or FP64) flops the method needs per launch of a sweep: 12 flops
-    per element-Givens (two complex rotations of an amplitude pair are 24
-    real FMA-flops per pair), N(N-1)/2 rotations each touching the fraction
-    2 C(N-2, n-1) / C(N, n) of the strings; the reverse sweep rotates two
-    states and adds the transition reduction, n(N-n) + n complex
-    multiply-adds (8 flops) per amplitude and spin."""
+    """FP32 (or FP64) flops the method needs per launch of a sweep: 10 real
+    flops per element-Givens (x' = c x + s y: 2 for c x, 6 for the complex
+    product s y, 2 for the sum), N(N-1)/2 rotations each touching the
+    fraction 2 C(N-2, n-1) / C(N, n) of the strings; the reverse sweep
+    rotates two states and adds the transition reduction, n(N-n) + n
+    complex multiply-adds (8 flops) per amplitude and spin."""
     spin = 0 if "alpha" in kernel else 1
     n = nelec[spin]
     N = norb
     if not kernel.startswith("sweep") or n < 1 or N < 2:
         return None
     eg = N * (N - 1) / 2 * 2 * math.comb(N - 2, n - 1) / math.comb(N, n)
-    per = 12 * eg
+    per = FLOPS_PER_ELEMENT_GIVENS * eg
     if "vjp" in kernel:
         per = 2 * per + 8 * (n * (N - n) + n)
     return per * amplitudes
@@ -213,6 +216,13 @@ def run_gpu(args):
         fsgpu.lucj_forward_(vec, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
         return fsgpu.lucj_vjp_(vec, cot, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
 
+    # the FP32 FMA pipe's measured rate (library probe kernel), before the
+    # workload so that it runs on a cool GPU either way
+    fma_probe = None
+    try:
+        fma_probe = fsgpu.measure_fp32_fma(local)[0]
+    except fsgpu.FsError:
+        pass
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -249,17 +259,30 @@ def run_gpu(args):
         side = torch.cuda.Stream()
         main = torch.cuda.current_stream()
 
-        def step_e2e():
+        phases = ("h2d", "forward", "vjp", "d2h")
+        marks = []
+
+        def step_e2e(ev=None):
             # the cotangent is needed only by the VJP: its copy runs on a
             # side stream under the forward pass
             side.wait_stream(main)
             with torch.cuda.stream(side):
                 dc.copy_(hc, non_blocking=True)
+            if ev:
+                ev[0].record(main)
             dv.copy_(hv, non_blocking=True)
+            if ev:
+                ev[1].record(main)
             fsgpu.lucj_forward_(dv, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+            if ev:
+                ev[2].record(main)
             main.wait_stream(side)
             g = fsgpu.lucj_vjp_(dv, dc, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+            if ev:
+                ev[3].record(main)
             hout.copy_(dc, non_blocking=True)
+            if ev:
+                ev[4].record(main)
             main.synchronize()
             return g
 
@@ -267,17 +290,27 @@ def run_gpu(args):
             step_e2e()
         torch.cuda.synchronize()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps + 1)]
+        ctx.profile_start()
         evs[0].record()
         for k in range(args.e2e_steps):
             step_e2e()
             evs[k + 1].record()
         torch.cuda.synchronize()
+        eprof = ctx.profile_stop()
         each = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.e2e_steps)]
         ems = max_over_ranks(evs[0].elapsed_time(evs[-1]) / args.e2e_steps, dist, "cuda")
+        # one more step, instrumented phase by phase (outside the timed steps)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        step_e2e(pe)
+        torch.cuda.synchronize()
+        breakdown = {ph: pe[i].elapsed_time(pe[i + 1]) for i, ph in enumerate(phases)}
         grad_bytes = K.size * 16 + Jaa.size * 8 + Jab.size * 8
         e2e = {"value": job_throughput(world, NLAYERS, ems), "unit": "layers/s",
                "h2d_bytes_per_step": 2 * S, "d2h_bytes_per_step": S + grad_bytes,
-               "ms_per_step": ems, "ms_each_step": each}
+               "ms_per_step": ems, "ms_each_step": each,
+               "phase_ms_one_step": breakdown,
+               "kernel_ms_per_step": sum(v[1] for v in eprof.values()) / args.e2e_steps,
+               "device_timed_kernel_ms_per_step": sum(v[1] for v in prof.values()) / args.steps}
 
     # complex128, same workload, plain path on the same GPU
     c128 = None
@@ -327,14 +360,19 @@ def run_gpu(args):
         if fl is not None and csum:
             # The fused sweeps move each amplitude once per launch and are
             # bound by FP32 arithmetic: the roofline is the FP32 FMA peak from
-            # the unit counts (152 SMs x 128 lanes x 2 flops per clock) at the
-            # SM clock sampled during the timed region; the HBM view is kept
-            # beside it.
-            fpeak = 152 * 128 * 2 * csum["sm_mhz"] * 1e6 / 1e12
+            # the unit counts (SMs of this device x 128 FP32 lanes x 2 flops
+            # per clock) at the SM clock sampled during the timed region; the
+            # library's FMA-throughput probe and the HBM view are kept beside
+            # it.
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            fpeak = sms * 128 * 2 * csum["sm_mhz"] * 1e6 / 1e12
             fach = fl / (per_launch_ms / 1e3) / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": fach, "peak": fpeak,
-                    "peak_source": "unit counts x sampled SM clock (FP32 FMA)",
+                    "peak_source": "unit counts x sampled SM clock (FP32 FMA), %d SMs" % sms,
+                    "peak_fp32_fma_probe": fma_probe,
+                    "frac_of_probe": fach / fma_probe if fma_probe else None,
                     "unit": "TFLOP/s", "frac": fach / fpeak, "traffic": tr,
+                    "flops_per_element_givens": FLOPS_PER_ELEMENT_GIVENS,
                     "algorithmic_flops_per_launch": fl, "ms_per_launch": per_launch_ms,
                     "share_of_step": tot_ms / ms, "hbm": hbm}
         else:
@@ -368,6 +406,17 @@ def run_gpu(args):
             out["trotter"] = run_trotter(args, ctx)
             out["operator_action"] = run_operator_action(args, ctx)
             out["sampling"] = run_sampling(args, ctx)
+    if c128:
+        out["c128_layers_per_s"] = c128["layers_per_s"]
+        out["c64_speedup_vs_c128"] = c128["c64_speedup"]
+    if out.get("batch"):
+        b = out["batch"]
+        out["batch_circuits_per_s"] = b["circuits_per_s"]
+        out["batch_c64_speedup_vs_plain_c128"] = b["c64_batched_speedup_vs_plain_c128"]
+        out["batch_speedup_vs_plain_c64"] = b["circuits_per_s"] / b["plain_c64_circuits_per_s_equiv"]
+    if out.get("largest"):
+        out["largest_fwd_vjp_ms"] = out["largest"]["fwd_vjp_ms"]
+        out["largest_fwd_ms_c128"] = out["largest"]["fwd_ms_c128"]
     if rank == 0 and not args.no_cpu_baseline and not args.norb:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -718,74 +767,187 @@ def run_small_rotation(args, ctx):
 
 
 # ------------------------------------------------------------------ oracle
-def cpu_baseline(w, budget_s=None):
-    """The oracle, as it stands, on a bounded sample of the workload, scaled
-    to layers/s by the oracle's own gate count per layer.
+# The oracle's LUCJ reverse mode per layer applies 4 orbital rotations
+# (U^dag and U forward, both again on the cotangent), each N(N-1)/2 = 120
+# Givens rotations per spin from its own decomposition; 2 transition one-body
+# reductions (one per rotation gate); 2 diagonal-Coulomb phase evaluations.
+GIVENS_PER_LAYER_PER_SPIN = 4 * 120
+T_PER_LAYER = 2
+DC_PER_LAYER = 2
 
-    The oracle's LUCJ reverse mode per layer applies 4 orbital rotations
-    (U^dag and U forward, both again on the cotangent), each N(N-1)/2 = 120
-    Givens rotations per spin from its own decomposition; 2 transition
-    one-body reductions (one per rotation gate); 2 diagonal-Coulomb phase
-    evaluations.  Sample: 1 Givens rotation per spin on the full N=16
-    state, 1 diagonal-Coulomb evolution on the full state, and the
-    transition reduction on 16- and 32-vector slices of the state (alpha
-    part on column slices, beta part on row slices), extrapolated linearly
-    in the slice width."""
-    import oracle
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_slice_times(norb, nelec, width, seed):
+    """One worker's share of the oracle sample: on its own slice of `width`
+    columns (alpha operations) and `width` rows (beta operations) of the
+    N-orbital state (random values; the cost does not depend on them), time
+    one alpha and one beta Givens rotation and the transition one-body
+    reduction of both spins, as the oracle runs them.  Runs in a spawned
+    process (one host core)."""
     from oracle import gates, lucj
-
-    norb, nelec = NORB, NELEC
-    v = w["vec"]
-    c = w["cot"]
-    t0 = time.perf_counter()
-    # Givens rotations (pairs are enumerated once, as the oracle caches them)
-    gates.givens_pairs(norb, 8, 0, 5)
-    gates.givens_pairs(norb, 8, 3, 11)
-    tg = []
-    for spin, (p, q) in ((0, (0, 5)), (1, (3, 11))):
-        t = time.perf_counter()
-        gates.apply_givens(v, 0.6, 0.8j, p, q, spin, norb, nelec)
-        tg.append(time.perf_counter() - t)
+    from paper_2605_03123_gb300 import inputs
+    d = math.comb(norb, nelec[0])
+    g = inputs.rng(seed)
+    mk = lambda shape: g.standard_normal(shape) + 1j * g.standard_normal(shape)
+    vc, cc = mk((d, width)), mk((d, width))
+    vr, cr = mk((width, d)), mk((width, d))
+    gates.givens_pairs(norb, nelec[0], 0, 5)    # the oracle caches its pair lists
+    gates.givens_pairs(norb, nelec[1], 3, 11)
     t = time.perf_counter()
-    oracle.apply_diag_coulomb_evolution(v, w["J_aa"][0], w["J_ab"][0], None, 1.0, norb, nelec)
-    tdc = time.perf_counter() - t
-    tt = []
-    for k in (16, 32):
+    gates.apply_givens(vc, 0.6, 0.8j, 0, 5, 0, norb, nelec)
+    t_ga = time.perf_counter() - t
+    t = time.perf_counter()
+    gates.apply_givens(vr, 0.6, 0.8j, 3, 11, 1, norb, nelec)
+    t_gb = time.perf_counter() - t
+    t = time.perf_counter()
+    lucj.transition_one_body(cc, vc, norb, nelec, spins=(0,))
+    lucj.transition_one_body(cr, vr, norb, nelec, spins=(1,))
+    t_T = time.perf_counter() - t
+    return t_ga, t_gb, t_T
+
+
+SLICE_WIDTHS = (32, 64)
+
+
+def oracle_slice_work(norb, nelec, seed):
+    """One host process's share of the oracle sample: oracle_slice_times at
+    the two SLICE_WIDTHS (the transition reduction has a fixed cost for its
+    pair lists plus a part linear in the width; the Givens rotations are
+    linear in the width)."""
+    return [oracle_slice_times(norb, nelec, wd, seed + wd) for wd in SLICE_WIDTHS]
+
+
+def _project(times, width):
+    """Phase times of a (width)-wide slice from the two measured widths."""
+    (a, b) = SLICE_WIDTHS
+    ta, tb = times
+    slope = (tb[2] - ta[2]) / (b - a)
+    return (tb[0] * width / b, tb[1] * width / b, max(tb[2] + slope * (width - b), tb[2]))
+
+
+def oracle_layer_sample(w, workers):
+    """One bounded sample of the oracle on `workers` host processes plus the
+    parent.  Every worker, concurrently, times one alpha and one beta Givens
+    rotation and the transition reduction of both spins on its own 32- and
+    64-vector column and row slices of the N=16 state; the parent meanwhile
+    applies one diagonal-Coulomb evolution to the whole state.  With the
+    state split evenly over the workers (d / workers vectors each), a
+    worker's phase times follow from its two widths (linear in the width,
+    plus the reduction's fixed cost, which every worker pays); each phase
+    takes the slowest worker's time.  A layer is GIVENS_PER_LAYER_PER_SPIN
+    of each Givens phase, T_PER_LAYER reductions and DC_PER_LAYER
+    evolutions.  Returns (layer seconds, measured sample seconds, phases)."""
+    import concurrent.futures
+    import multiprocessing
+    import oracle
+    norb, nelec = NORB, NELEC
+    d = math.comb(norb, nelec[0])
+    share = d / workers
+    t0 = time.perf_counter()
+    if workers == 1:
+        res = [oracle_slice_work(norb, nelec, 77)]
         t = time.perf_counter()
-        lucj.transition_one_body(c[:, :k], v[:, :k], norb, nelec, spins=(0,))
-        lucj.transition_one_body(c[:k, :], v[:k, :], norb, nelec, spins=(1,))
-        tt.append(time.perf_counter() - t)
-    # per-column slope and intercept of the reduction cost
-    slope = (tt[1] - tt[0]) / 16
-    t_T = max(tt[0] + slope * (math.comb(norb, 8) - 16), tt[1])
-    per_layer = 4 * 120 * (tg[0] + tg[1]) + 2 * t_T + 2 * tdc
-    return {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle",
-            "sample": ("1 Givens rotation per spin and 1 diagonal-Coulomb evolution on "
-                       "the full N=16 (8,8) complex128 state; the transition reduction on "
-                       "16- and 32-vector slices per spin, extrapolated linearly; composed "
-                       "by the oracle's per-layer gate count"),
-            "sample_seconds": time.perf_counter() - t0}
+        oracle.apply_diag_coulomb_evolution(w["vec"], w["J_aa"][0], w["J_ab"][0], None, 1.0,
+                                            norb, nelec)
+        t_dc = time.perf_counter() - t
+    else:
+        ctx = multiprocessing.get_context("spawn")
+        with concurrent.futures.ProcessPoolExecutor(workers, mp_context=ctx) as ex:
+            futs = [ex.submit(oracle_slice_work, norb, nelec, 77 + 1000 * k)
+                    for k in range(workers)]
+            t = time.perf_counter()
+            oracle.apply_diag_coulomb_evolution(w["vec"], w["J_aa"][0], w["J_ab"][0], None,
+                                                1.0, norb, nelec)
+            t_dc = time.perf_counter() - t
+            res = [f.result() for f in futs]
+    wall = time.perf_counter() - t0
+    proj = [_project(r, share) for r in res]
+    t_ga = max(p[0] for p in proj)
+    t_gb = max(p[1] for p in proj)
+    t_T = max(p[2] for p in proj)
+    layer = (GIVENS_PER_LAYER_PER_SPIN * (t_ga + t_gb) + T_PER_LAYER * t_T
+             + DC_PER_LAYER * t_dc)
+    return layer, wall, {"givens_alpha_s": t_ga, "givens_beta_s": t_gb,
+                         "transition_s": t_T, "diag_coulomb_s": t_dc}
+
+
+def default_workers():
+    """Host processes for the all-core sample: one per core beside the
+    parent."""
+    return max(1, (os.cpu_count() or 2) - 1)
+
+
+SAMPLE_TEXT = ("%d host process(es), concurrently, each time one alpha and one beta Givens "
+               "rotation and the transition reduction of both spins on 32- and 64-vector "
+               "slices of the N=16 (8,8) complex128 state, projected to a 1/%d share of the "
+               "state, while the parent times one diagonal-Coulomb evolution of the whole "
+               "state; a layer is 480 Givens rotations per spin, 2 reductions and 2 "
+               "evolutions (the oracle's gate count)")
+
+
+def cpu_baseline(w):
+    """The oracle, as it stands, on bounded samples of the workload: on all
+    host cores (spawned workers) and on one core, each scaled to layers/s
+    by the oracle's own gate count per layer."""
+    one, wall1, parts1 = oracle_layer_sample(w, 1)
+    nw = default_workers()
+    allc, wall, parts = oracle_layer_sample(w, nw)
+    return {"value": 1.0 / allc, "unit": "layers/s", "cores": nw + 1, "kind": "oracle",
+            "cpu_model": cpu_model(), "logical_cpus": os.cpu_count(), "projected": True,
+            "sample": SAMPLE_TEXT % (nw, nw),
+            "sample_seconds": wall, "phases_s": parts,
+            "single_core": {"value": 1.0 / one, "unit": "layers/s", "cores": 1,
+                            "sample": SAMPLE_TEXT % (1, 1),
+                            "sample_seconds": wall1, "phases_s": parts1}}
 
 
 def run_reference(args):
+    """The oracle arm: each step is one all-core bounded sample; `value` is
+    the layer rate it implies, `ms_per_step` the time the sample itself
+    took."""
     rank = env_int("RANK", 0)
     if rank != 0:
         return
     w = workload()
-    vals = []
+    nw = default_workers()
+    rates, walls, parts = [], [], None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(w)
+        layer, wall, parts_i = oracle_layer_sample(w, nw)
         if i >= args.warmup:
-            vals.append(r)
-    v = statistics.median(x["value"] for x in vals)
+            rates.append(1.0 / layer)
+            walls.append(wall)
+            parts = parts_i
+    v = statistics.median(rates)
+    ms_step = 1e3 * sum(walls) / len(walls)
+    sample = "per step: " + SAMPLE_TEXT % (nw, nw)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "layers/s",
            "n_gpus": env_int("WORLD_SIZE", 1), "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": ms_step, "projected": True,
+           "projected_ms_per_layer": 1e3 / v,
+           "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "norb": NORB, "nelec": list(NELEC),
                       "layers": NLAYERS},
-           "cpu_baseline": {"value": v, "unit": "layers/s", "cores": 1, "kind": "oracle",
-                            "sample": vals[0]["sample"]},
+           "cpu_baseline": {"value": v, "unit": "layers/s", "cores": nw + 1, "kind": "oracle",
+                            "cpu_model": cpu_model(), "sample": sample,
+                            "phases_s": parts},
            "e2e": {"value": v, "unit": "layers/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

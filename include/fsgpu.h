@@ -103,6 +103,31 @@ int fs_profile_stop(fs_ctx *ctx, char *out, int64_t cap);
  * FS_ERR_UNSUPPORTED. */
 int fs_set_rotation_path(fs_ctx *ctx, int path);
 
+/* Arithmetic engine of the complex64 Givens sweeps (§3.2.3).
+ *   FS_SWEEP_AUTO:      the CUDA cores (measured faster on GB300 at the
+ *                       benchmarked sectors, see FS_SWEEP_TENSOR);
+ *   FS_SWEEP_CUDA_CORE: every Givens rotation as FP32 FMAs on CUDA cores;
+ *   FS_SWEEP_TENSOR:    each window step of 6 adjacent orbitals as one
+ *                       dense product with the compound matrices of the
+ *                       step (det V[S', S], §2.3) on the tcgen05 tensor
+ *                       cores, both operands split exactly into three
+ *                       BF16 pieces and six products kept (FP32
+ *                       accuracy); falls back to the CUDA cores where the
+ *                       tensor path does not apply (complex128, fewer than
+ *                       6 orbitals, vectors spanning more than 2 CTAs).
+ * Results agree to FP32 rounding.  FS_ERR_ARG for another value. */
+enum { FS_SWEEP_AUTO = 0, FS_SWEEP_CUDA_CORE = 1, FS_SWEEP_TENSOR = 2 };
+int fs_set_sweep_engine(fs_ctx *ctx, int engine);
+
+/* Measures the device's FP32 fused multiply-add throughput (the denominator
+ * of the arithmetic roofline of the Givens sweeps): 8 blocks of 256 threads
+ * per SM, each thread running 8 independent FMA chains, timed with CUDA
+ * events on `stream` after two warm-up launches.  Writes TFLOP/s (2 flops
+ * per FMA) to *tflops and, if ms is not NULL, the time of one launch.
+ * Synchronizes `stream`; allocates a small result buffer with
+ * cudaMallocAsync.  Not part of the paper's method: a measurement aid. */
+int fs_measure_fp32_fma(void *stream, double *tflops, double *ms);
+
 /* Sector string tables, built on the device with the combinatorial number
  * system (§3.1 addressing).  Copies dim = C(norb, nocc) masks to
  * `masks_host` (caller-owned, dim entries) in address order.

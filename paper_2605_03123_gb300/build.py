@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libfsgpu.so"
 SOURCES = ["fs_api.cu", "fs_tables.cu", "fs_sweep.cu", "fs_reduce.cu", "fs_minor.cu",
-           "fs_phase_tc.cu", "fs_batch.cu", "fs_operator.cu", "fs_noalloc.cu", "fs_sample.cu",
+           "fs_phase_tc.cu", "fs_batch.cu", "fs_operator.cu", "fs_noalloc.cu", "fs_sample.cu", "fs_peak.cu",
            "fs_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -552,6 +552,15 @@ int fs_set_rotation_path(fs_ctx* ctx, int path) {
   });
 }
 
+int fs_set_sweep_engine(fs_ctx* ctx, int engine) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    FS_REQUIRE(engine >= FS_SWEEP_AUTO && engine <= FS_SWEEP_TENSOR, FS_ERR_ARG,
+               "unknown sweep engine");
+    ctx->sweep_engine = engine;
+  });
+}
+
 int fs_string_table(fs_ctx* ctx, int norb, int nocc, uint32_t* masks_host, int64_t dim) {
   return guarded([&] {
     FS_REQUIRE(ctx != nullptr && masks_host != nullptr, FS_ERR_ARG, "null pointer");

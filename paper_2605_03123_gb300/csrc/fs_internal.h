@@ -77,6 +77,18 @@ void window_groups_host(const std::vector<uint32_t>& orbits, const std::vector<i
                         const std::vector<uint8_t>& okey, int b, std::vector<uint32_t>& gorb,
                         std::vector<int>& goff);
 
+// One segment of the gather indices of the tensor-core window steps: for a
+// window position (and, for a cluster, one rank's orbits), the orbits of the
+// classes m = 3, 2, 4, 1, 5 in that order, each orbit a row of its C(6, m)
+// string addresses (ascending local masks) padded to a multiple of 8;
+// idx[start .. start + len) in uint16 units (both multiples of 8), cnt[i]
+// orbits of the i-th class.
+struct TcSeg {
+  int start, len;
+  int cnt[5];
+  int pad_;
+};
+
 // Device copy of a pass: the subset, the owned slots, the record range.
 struct TPassDev {
   int q[4];
@@ -137,6 +149,11 @@ struct Space {
     // the host copies
     uint32_t* gorb[4] = {};
     int* goff[4] = {};
+    // gather indices of the tensor-core steps (W = 6 only), for the whole
+    // orbit list (b = 0) and for the rank groups of 2-CTA clusters (b = 1)
+    TcSeg* tc_seg[2] = {};
+    uint16_t* tc_idx[2] = {};
+    int tc_seg_max[2] = {};  // largest segment, bytes
     std::vector<uint32_t> orb_h;
     std::vector<int> off_h;
     std::vector<uint8_t> okey_h;
@@ -178,6 +195,7 @@ struct Ctx {
   std::vector<ProfRec> prof;
   cudaDeviceProp prop{};
   int rot_path = FS_ROT_AUTO;
+  int sweep_engine = FS_SWEEP_AUTO;
   std::map<std::pair<int, int>, Space*> spaces;
   std::map<std::string, Scratch> scratch;
   int* d_status = nullptr;  // device status word
@@ -346,6 +364,17 @@ struct SweepGeom {
   const int* tgoff;
   const uint16_t* offs;    // [npos][nocc + 1][1 << W] in-window rank offsets
   int offs_stride;         // (nocc + 1) << W
+  // tensor-core window steps (W = 6): per step the B images of classes
+  // m = 1..5 (tc::kStepBytes each step); gather-index segments per window
+  // position (seg_full[a]) and, for blocked clusters, per position and rank
+  // (seg_grp[a * 2 + rank]); idx_cap = bytes of one staged segment buffer
+  const unsigned char* tc_b;
+  const TcSeg* tc_seg_full;
+  const uint16_t* tc_idx_full;
+  const TcSeg* tc_seg_grp;
+  const uint16_t* tc_idx_grp;
+  int tc_idx_cap;
+  int* status;  // device status word (bounded waits that gave up)
 };
 
 struct SweepJob {

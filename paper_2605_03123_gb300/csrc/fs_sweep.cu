@@ -16,8 +16,11 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "fs_common.cuh"
 #include "fs_internal.h"
+#include "fs_tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -103,6 +106,368 @@ template <int W, int M, int... K>
 __device__ __forceinline__ void win_offsets(const uint16_t* Fc, int (&e)[sizeof...(K)],
                                             std::integer_sequence<int, K...>) {
   ((e[K] = win_offset<W, M, K>(Fc)), ...);
+}
+
+// ------------------------------------------- tensor-core window steps
+// Per-CTA state of the tensor-core steps (see fs_tc.cuh).
+struct TcCtx {
+  uint32_t tbase;      // TMEM base of the CTA (lane 0, column 0)
+  uint32_t bsm[2];     // shared-memory addresses of the two step-image buffers
+  uint32_t mbar_b[2];  // their bulk-copy mbarriers
+  uint32_t mbar_mma;   // this warpgroup's MMA-completion mbarrier
+  uint32_t ph_mma;     // its next phase parity
+  int wg, wq, lane;    // warpgroup, warp within it, lane
+  int* status;
+};
+
+__device__ __forceinline__ void tc_timeout(int* status) {
+  if (status) atomicCAS(status, 0, (int)FS_ERR_TIMEOUT);
+}
+
+// Gather-index row length of class M (C(6, M) addresses padded to 8).
+template <int M>
+constexpr int tc_pad() {
+  return (cbinom(tc::kW, M) + 7) / 8 * 8;
+}
+
+// One tile of class M: rows [row0, row0 + 128) of the class's rows
+// [.., row_end); row = (state s, vector kv, orbit o) with o fastest, and
+// orbit o's string addresses are row o of the class's gather indices `ix`
+// (shared memory).  Every thread of the warpgroup runs this (the tcgen05
+// loads and stores are warp-collective); rows past row_end load zeros and
+// store nothing.
+template <int M, int CS>
+__device__ __forceinline__ void tc_tile(TcCtx& t, int row0, int row_end, int count, int kv_eff,
+                                        int KV, size_t st_stride, const uint16_t* ix,
+                                        cx_t<float>* const* base, const int (&cbr)[CS + 1],
+                                        int buf, uint32_t ph_b, bool& b_ready) {
+  using C = cx_t<float>;
+  constexpr int NS = cbinom(tc::kW, M);
+  constexpr int KP = tc::kp(M);
+  constexpr int PAD = tc_pad<M>();
+  const uint32_t col0 = t.tbase + (uint32_t)(t.wg * tc::kWgCols);
+  const uint32_t lanes = (uint32_t)(t.wq * 32) << 16;
+  const int row = row0 + t.wq * 32 + t.lane;
+  const bool valid = row < row_end;
+  int ad[NS];
+  int own[CS > 1 ? NS : 1];
+  if (valid) {
+    const int per = kv_eff * count;
+    const int s = row / per;
+    const int rem = row - s * per;
+    const int kv = rem / count;
+    const int o = rem - kv * count;
+    uint32_t w[PAD / 2];
+    const uint4* src = reinterpret_cast<const uint4*>(ix + o * PAD);
+#pragma unroll
+    for (int q = 0; q < PAD / 8; ++q) {
+      const uint4 u = src[q];
+      w[4 * q] = u.x;
+      w[4 * q + 1] = u.y;
+      w[4 * q + 2] = u.z;
+      w[4 * q + 3] = u.w;
+    }
+    const int sbase = (int)(s * st_stride) + kv;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int e = (int)((w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+      int b0 = 0;
+      if constexpr (CS > 1) {
+        int r0 = 0;
+#pragma unroll
+        for (int r = 1; r < CS; ++r)
+          if (e >= cbr[r]) {
+            r0 = r;
+            b0 = cbr[r];
+          }
+        own[k] = r0;
+      }
+      ad[k] = sbase + (e - b0) * KV;
+    }
+  }
+  // gather, split, A = [x1 | x2 | x3] into this thread's TMEM lane, 4
+  // amplitudes (8 BF16 of K, 4 columns per piece) at a time; padding
+  // columns get zeros
+  constexpr int AC = tc::a_cols(M);
+#pragma unroll
+  for (int c = 0; c < AC / 4; ++c) {
+    uint32_t p1[4], p2[4], p3[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * c + j;
+      C x = mk<float>(0.f, 0.f);
+      if (k < NS && valid) x = base[CS > 1 ? own[k < NS ? k : 0] : 0][ad[k < NS ? k : 0]];
+      tc::split_bf16x3(x.x, x.y, p1[j], p2[j], p3[j]);
+    }
+    tc::tmem_st4(col0 + lanes + 4 * c, p1);
+    tc::tmem_st4(col0 + lanes + AC + 4 * c, p2);
+    tc::tmem_st4(col0 + lanes + 2 * AC + 4 * c, p3);
+  }
+  tc::wait_st();
+  tc::fence_before();
+  tc::wg_bar(1 + t.wg);
+  if (t.wq == 0 && t.lane == 0) {
+    tc::fence_after();
+    if (!b_ready) {
+      if (!tc::mbar_wait(t.mbar_b[buf], ph_b)) tc_timeout(t.status);
+      b_ready = true;
+    }
+    const uint32_t b0 = t.bsm[buf] + tc::class_offset(M);
+    constexpr uint32_t SBO = (KP / 8) * 128;
+    constexpr uint32_t ID = tc::idesc(M);
+    const uint32_t d = col0 + tc::kPieces * AC;
+    // the six products A_i B_j (i + j <= 4 over pieces 1..3), smallest first
+    constexpr int kA[6] = {2, 1, 0, 1, 0, 0};
+    constexpr int kB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+    for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+      for (int ks = 0; ks < KP / 16; ++ks) {
+        const uint64_t bd = tc::sdesc(b0 + kB[pr] * tc::piece_bytes(M) + ks * 256, 128, SBO);
+        tc::mma_bf16(d, col0 + kA[pr] * AC + 8 * ks, bd, ID, (pr > 0 || ks > 0) ? 1u : 0u);
+      }
+    tc::mma_commit(t.mbar_mma);
+  }
+  __syncwarp();
+  if (!tc::mbar_wait(t.mbar_mma, t.ph_mma)) tc_timeout(t.status);
+  t.ph_mma ^= 1u;
+  tc::fence_after();
+  // D row back to the slab: all loads of the row, one wait, then the stores
+  // (which the wait's memory clobber keeps after it)
+  constexpr int NC = (2 * NS + 7) / 8;
+  uint32_t v[NC][8];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) tc::tmem_ld8(col0 + lanes + tc::kPieces * AC + 8 * c, v[c]);
+  tc::wait_ld();
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * c + j;
+      if (k < NS && valid)
+        base[CS > 1 ? own[k < NS ? k : 0] : 0][ad[k < NS ? k : 0]] =
+            mk<float>(__uint_as_float(v[c][2 * j]), __uint_as_float(v[c][2 * j + 1]));
+    }
+}
+
+// The tiles of class M (the i-th class of the step) that fall to this
+// warpgroup: tiles are numbered across the classes of the step from
+// `tile_base` and dealt round-robin over the warpgroups.
+template <int M, int CS, int NST>
+__device__ __forceinline__ void tc_class(TcCtx& t, const TcSeg& sg, int i, int& ioff,
+                                         int& tile_base, bool split_rows, int rank, int kv_eff,
+                                         int KV, size_t st_stride, const uint16_t* six,
+                                         cx_t<float>* const* base, const int (&cbr)[CS + 1],
+                                         int buf, uint32_t ph_b, bool& b_ready) {
+  const int count = sg.cnt[i];
+  const int rows = NST * kv_eff * count;
+  int lo = 0, hi = rows;
+  if (CS > 1 && split_rows) {  // rows shared out over the cluster
+    lo = (int)((int64_t)rows * rank / CS);
+    hi = (int)((int64_t)rows * (rank + 1) / CS);
+  }
+  const int nt = (hi - lo + tc::kRows - 1) / tc::kRows;
+  const uint16_t* ix = six + ioff;
+  for (int tl = ((t.wg - tile_base) % tc::kWg + tc::kWg) % tc::kWg; tl < nt; tl += tc::kWg)
+    tc_tile<M, CS>(t, lo + tl * tc::kRows, hi, count, kv_eff, KV, st_stride, ix, base, cbr, buf,
+                   ph_b, b_ready);
+  tile_base += nt;
+  ioff += count * tc_pad<M>();
+}
+
+// All window steps of a program on the tensor cores, for the CTA's part of
+// the slab(s).  `bsm` (128-byte aligned shared memory) holds two step images
+// and then two gather-index buffers of g.tc_idx_cap bytes; step st + 1's
+// image and indices are copied in while step st runs.  Ends with every
+// bulk copy complete and the TMEM freed.
+template <int CS, int NST>
+__device__ void tc_window_steps(const SweepGeom& g, const WProg<float>& prog,
+                                cx_t<float>* const* base, const int (&cbr)[CS + 1], int KV,
+                                int kv_eff, size_t st_stride, int rank, unsigned char* bsm) {
+  __shared__ __align__(8) uint64_t s_mbar[2 + tc::kWg];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  TcCtx t;
+  t.wg = warp >> 2;
+  t.wq = warp & 3;
+  t.lane = tid & 31;
+  t.status = g.status;
+  uint16_t* sidx[2] = {reinterpret_cast<uint16_t*>(bsm + 2 * tc::kStepBytes),
+                       reinterpret_cast<uint16_t*>(bsm + 2 * tc::kStepBytes + g.tc_idx_cap)};
+  if (tid == 0) {
+    for (int i = 0; i < 2 + tc::kWg; ++i) tc::mbar_init(tc::smem_u32(&s_mbar[i]), 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), tc::kTmemCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  t.tbase = s_tmem;
+  t.bsm[0] = tc::smem_u32(bsm);
+  t.bsm[1] = t.bsm[0] + tc::kStepBytes;
+  t.mbar_b[0] = tc::smem_u32(&s_mbar[0]);
+  t.mbar_b[1] = tc::smem_u32(&s_mbar[1]);
+  t.mbar_mma = tc::smem_u32(&s_mbar[2 + t.wg]);
+  t.ph_mma = 0;
+  const int nsteps = prog.nsteps;
+  // the segment of step st: this rank's orbits when the window is clear of
+  // the top orbitals of a blocked cluster, else the whole list
+  auto segment = [&](int st, const uint16_t*& idx) -> const TcSeg* {
+    const int a = prog.a[st];
+    if (CS > 1 && g.blocked && a + tc::kW <= g.norb - g.lgcs) {
+      idx = g.tc_idx_grp;
+      return g.tc_seg_grp + a * CS + rank;
+    }
+    idx = g.tc_idx_full;
+    return g.tc_seg_full + a;
+  };
+  auto stage = [&](int st, int b) {  // thread 0: step st's image and indices into buffer b
+    const uint16_t* idx;
+    const TcSeg* sp = segment(st, idx);
+    const int start = __ldg(&sp->start), len = __ldg(&sp->len);
+    tc::mbar_expect_tx(t.mbar_b[b], tc::kStepBytes + 2u * (uint32_t)len);
+    tc::bulk_g2s(t.bsm[b], g.tc_b + (size_t)st * tc::kStepBytes, tc::kStepBytes, t.mbar_b[b]);
+    if (len > 0)
+      tc::bulk_g2s(tc::smem_u32(sidx[b]), idx + start, 2u * (uint32_t)len, t.mbar_b[b]);
+  };
+  if (tid == 0 && nsteps > 0) stage(0, 0);
+  for (int st = 0; st < nsteps; ++st) {
+    const int buf = st & 1;
+    const uint32_t ph_b = (uint32_t)(st >> 1) & 1u;
+    if (tid == 0 && st + 1 < nsteps) {  // the other buffer's last readers are done
+      // its previous copy (step st - 1) has landed before it is reused
+      if (st >= 1 && !tc::mbar_wait(t.mbar_b[buf ^ 1], (uint32_t)((st - 1) >> 1) & 1u))
+        tc_timeout(t.status);
+      stage(st + 1, buf ^ 1);
+    }
+    // every thread reads this step's gather indices: wait for them
+    if (!tc::mbar_wait(t.mbar_b[buf], ph_b)) tc_timeout(t.status);
+    bool b_ready = true;
+    const uint16_t* idx_unused;
+    const TcSeg sg = *segment(st, idx_unused);
+    const bool split_rows = !(CS > 1 && g.blocked && prog.a[st] + tc::kW <= g.norb - g.lgcs);
+    int ioff = 0, tile_base = 0;
+    tc_class<3, CS, NST>(t, sg, 0, ioff, tile_base, split_rows, rank, kv_eff, KV, st_stride, sidx[buf], base, cbr, buf, ph_b, b_ready);
+    tc_class<2, CS, NST>(t, sg, 1, ioff, tile_base, split_rows, rank, kv_eff, KV, st_stride, sidx[buf], base, cbr, buf, ph_b, b_ready);
+    tc_class<4, CS, NST>(t, sg, 2, ioff, tile_base, split_rows, rank, kv_eff, KV, st_stride, sidx[buf], base, cbr, buf, ph_b, b_ready);
+    tc_class<1, CS, NST>(t, sg, 3, ioff, tile_base, split_rows, rank, kv_eff, KV, st_stride, sidx[buf], base, cbr, buf, ph_b, b_ready);
+    tc_class<5, CS, NST>(t, sg, 4, ioff, tile_base, split_rows, rank, kv_eff, KV, st_stride, sidx[buf], base, cbr, buf, ph_b, b_ready);
+    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+  }
+  // every bulk copy has landed (the buffers become the epilogue's tables),
+  // then the TMEM is freed
+  if (tid == 0 && nsteps > 0) {
+    for (int b = 0; b < 2 && b < nsteps; ++b) {
+      const int lst = ((nsteps - 1) & 1) == b ? nsteps - 1 : nsteps - 2;  // last step using b
+      if (!tc::mbar_wait(t.mbar_b[b], (uint32_t)(lst >> 1) & 1u)) tc_timeout(t.status);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(t.tbase, tc::kTmemCols);
+  }
+}
+
+// The B images of the tensor-core steps of one program, FP64 on the device:
+// per step, V = G_k ... G_1 (the step's Givens rotations in the window's
+// local orbitals, applied first to last), then for each class m the
+// compound matrix C_m(V)[S', S] = det V[S', S] in its real form
+// [[Re, -Im], [Im, Re]] (rows n = output reals, columns k = input reals,
+// re/im interleaved), split into three BF16 pieces (each the nearest BF16
+// of the remainder so far), K-major core matrices (see tc::b_offset).  One
+// block per step.
+__global__ void __launch_bounds__(256)
+    k_tc_bmats(const __grid_constant__ WProg<double> p, unsigned char* out) {
+  __shared__ double2 V[tc::kW * tc::kW];
+  const int st = blockIdx.x;
+  unsigned char* img = out + (size_t)st * tc::kStepBytes;
+  for (int i = threadIdx.x; i < tc::kStepBytes / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(img)[i] = 0u;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < tc::kW; ++i)
+      for (int j = 0; j < tc::kW; ++j) V[i * tc::kW + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int q = p.g0[st]; q < p.g0[st + 1]; ++q) {
+      const int u = p.u[q];
+      const double c = p.c[q], sr = p.sr[q], si = p.si[q];
+      for (int j = 0; j < tc::kW; ++j) {
+        const double2 x = V[u * tc::kW + j], y = V[(u + 1) * tc::kW + j];
+        // row u <- c x + s y, row u+1 <- -conj(s) x + c y
+        V[u * tc::kW + j] = make_double2(c * x.x + sr * y.x - si * y.y, c * x.y + sr * y.y + si * y.x);
+        V[(u + 1) * tc::kW + j] =
+            make_double2(-(sr * x.x + si * x.y) + c * y.x, -(sr * x.y - si * x.x) + c * y.y);
+      }
+    }
+  }
+  __syncthreads();
+  for (int m = 1; m < tc::kW; ++m) {
+    const int ns = tc::binom6(m), kpad = tc::kp(m);
+    for (int idx = threadIdx.x; idx < ns * ns; idx += blockDim.x) {
+      const int ip = idx / ns, iq = idx - ip * ns;
+      const int rm = win_mask(tc::kW, m, ip), cm = win_mask(tc::kW, m, iq);
+      double2 a[5 * 5];
+      int r = 0;
+      for (int i = 0; i < tc::kW; ++i) {
+        if (!((rm >> i) & 1)) continue;
+        int cc = 0;
+        for (int j = 0; j < tc::kW; ++j)
+          if ((cm >> j) & 1) a[r * m + (cc++)] = V[i * tc::kW + j];
+        ++r;
+      }
+      // det by Gaussian elimination with partial pivoting
+      double dr = 1, di = 0;
+      for (int k = 0; k < m; ++k) {
+        int piv = k;
+        double best = hypot(a[k * m + k].x, a[k * m + k].y);
+        for (int i = k + 1; i < m; ++i) {
+          const double h = hypot(a[i * m + k].x, a[i * m + k].y);
+          if (h > best) {
+            best = h;
+            piv = i;
+          }
+        }
+        if (best == 0) {
+          dr = di = 0;
+          break;
+        }
+        if (piv != k) {
+          for (int j = 0; j < m; ++j) {
+            const double2 tmp = a[k * m + j];
+            a[k * m + j] = a[piv * m + j];
+            a[piv * m + j] = tmp;
+          }
+          dr = -dr;
+          di = -di;
+        }
+        const double2 pk = a[k * m + k];
+        const double nr = dr * pk.x - di * pk.y;
+        di = dr * pk.y + di * pk.x;
+        dr = nr;
+        const double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
+        for (int i = k + 1; i < m; ++i) {
+          const double2 x = a[i * m + k];
+          const double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
+          for (int j = k + 1; j < m; ++j) {
+            const double2 y = a[k * m + j];
+            a[i * m + j].x -= fr * y.x - fi * y.y;
+            a[i * m + j].y -= fr * y.y + fi * y.x;
+          }
+        }
+      }
+      const double ent[4] = {dr, -di, di, dr};  // (2ip, 2iq), (2ip, 2iq+1), (2ip+1, 2iq), (2ip+1, 2iq+1)
+      for (int e = 0; e < 4; ++e) {
+        const int n = 2 * ip + (e >> 1), k = 2 * iq + (e & 1);
+        const int off = tc::b_offset(n, k, kpad);
+        double r = ent[e];
+        for (int pc = 0; pc < tc::kPieces; ++pc) {  // nearest BF16 of the remainder
+          const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
+          *reinterpret_cast<__nv_bfloat16*>(img + tc::class_offset(m) + pc * tc::piece_bytes(m) + off) = b;
+          r -= (double)__bfloat162float(b);
+        }
+      }
+    }
+  }
 }
 
 // One orbit of a window step: the C(W, M) strings sharing the occupation
@@ -372,7 +737,8 @@ __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
 // NT threads per CTA.  SPLIT (two states, no cluster): during the Givens
 // phase the first half of the CTA rotates state 0 and the second half state
 // 1, each half synchronising on its own named barrier.
-template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P>
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P,
+          bool TC = false>
 __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, const Mat& X,
                                            const int slab, const int rank,
                                            unsigned char* smraw) {
@@ -432,7 +798,16 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
   if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
 
   // ---- Givens rotations, in program order
-  if constexpr (W == 0) {
+  if constexpr (TC) {
+    static_assert(W == tc::kW && NT == tc::kThreads && !SPLIT && sizeof(R) == 4,
+                  "tensor-core steps: complex64, W = 6, 512 threads");
+    // the step images go after the slab(s), 128-byte aligned; the epilogue's
+    // tables reuse that space afterwards
+    const uint32_t s0 = tc::smem_u32(smraw);
+    const uint32_t sb = s0 + (uint32_t)(NST * st_stride * sizeof(C));
+    unsigned char* bsm = smraw + (((sb + 127u) & ~127u) - s0);
+    tc_window_steps<CS, NST>(g, prog, base, cbr, KV, kv_eff, st_stride, rank, bsm);
+  } else if constexpr (W == 0) {
     const int items = g.npp << g.lgKV;
     const int per = (items + CS - 1) / CS;
     const int lo = rank * per, hi = min(items, lo + per);
@@ -746,13 +1121,14 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
   }
 }
 
-template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT>
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, bool TC = false>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
             const __grid_constant__ Mat X) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  sweep_body<R, CS, NST, VJP, W, NT, SPLIT>(g, prog, X, blockIdx.x / CS, rank, smraw);
+  sweep_body<R, CS, NST, VJP, W, NT, SPLIT, typename ProgOf<R, W, (W > 0)>::type, TC>(
+      g, prog, X, blockIdx.x / CS, rank, smraw);
 }
 
 // Batched sweep: one persistent launch over the slabs of many jobs (one job
@@ -895,10 +1271,11 @@ static GProg<R> make_prog(const RotProgram& rp) {
   return p;
 }
 
-template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P>
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P,
+          bool TC = false>
 static void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
                            int nslabs, size_t smem, cudaStream_t st) {
-  auto kern = k_sweep<R, CS, NST, VJP, W, NT, SPLIT>;
+  auto kern = k_sweep<R, CS, NST, VJP, W, NT, SPLIT, TC>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   static const char* names[2][2][2] = {  // [f64][reverse][beta]
@@ -959,6 +1336,102 @@ static void set_window_geom(SweepGeom& g, Space* sp, int W) {
 // split mode (one half-CTA per state) unless the vector spans a cluster (in a
 // cluster the joint form measured faster: the split form gains little when
 // every step ends on the cluster barrier).
+// Gather indices of the tensor-core steps (see TcSeg), built once per space:
+// b = 0 for the whole orbit list of each window position, b = 1 for the two
+// rank groups of 2-CTA blocked clusters.  Row o of class m holds the
+// addresses R_O + F[a][c_lo][S] of the orbit's strings, S in ascending
+// local-mask order (the order of the compound matrices).
+static void build_tc_index(Space* sp, int b) {
+  Space::Win& wt = sp->win[tc::kW];
+  if (wt.tc_seg[b]) return;
+  const int W = tc::kW, N = sp->norb, n = sp->nocc;
+  const int npos = N - W + 1;
+  const int ranks = 1 << b;
+  // in-window rank offsets F, as in window_tables_host
+  std::vector<uint32_t> orbits;
+  std::vector<int> off;
+  std::vector<uint16_t> offs;
+  std::vector<uint8_t> okey;
+  window_tables_host(N, n, W, orbits, off, offs, okey);
+  std::vector<uint32_t> gorb;
+  std::vector<int> goff;
+  if (b > 0) window_groups_host(orbits, off, okey, b, gorb, goff);
+  static const int order[5] = {3, 2, 4, 1, 5};
+  std::vector<uint16_t> idx;
+  std::vector<TcSeg> seg((size_t)npos * ranks);
+  int mx = 0;
+  for (int a = 0; a < npos; ++a)
+    for (int r = 0; r < ranks; ++r) {
+      const uint32_t* list = b ? gorb.data() : orbits.data();
+      const int lo = b ? goff[a * 9 + r] : off[a], hi = b ? goff[a * 9 + r + 1] : off[a + 1];
+      TcSeg& sg = seg[(size_t)a * ranks + r];
+      sg.start = (int)idx.size();
+      for (int i = 0; i < 5; ++i) {
+        const int m = order[i];
+        const int ns = (int)cbinom(W, m), pad = (ns + 7) / 8 * 8;
+        int cnt = 0;
+        for (int k = lo; k < hi; ++k) {
+          const uint32_t desc = list[k];
+          if ((int)(desc >> 24) != m) continue;
+          const int RO = desc & 0xFFFF, clo = (desc >> 16) & 0xFF;
+          const uint16_t* Fc = offs.data() + (((size_t)a * (n + 1) + clo) << W);
+          for (int j = 0; j < pad; ++j)
+            idx.push_back(j < ns ? (uint16_t)(RO + Fc[win_mask(W, m, j)]) : (uint16_t)0);
+          ++cnt;
+        }
+        sg.cnt[i] = cnt;
+      }
+      while (idx.size() % 8) idx.push_back(0);
+      sg.len = (int)idx.size() - sg.start;
+      sg.pad_ = 0;
+      mx = std::max(mx, 2 * sg.len);
+    }
+  FS_CUDA(cudaMalloc(&wt.tc_idx[b], std::max<size_t>(idx.size(), 8) * sizeof(uint16_t)));
+  if (!idx.empty())
+    FS_CUDA(cudaMemcpy(wt.tc_idx[b], idx.data(), idx.size() * sizeof(uint16_t),
+                       cudaMemcpyHostToDevice));
+  FS_CUDA(cudaMalloc(&wt.tc_seg[b], seg.size() * sizeof(TcSeg)));
+  FS_CUDA(cudaMemcpy(wt.tc_seg[b], seg.data(), seg.size() * sizeof(TcSeg),
+                     cudaMemcpyHostToDevice));
+  wt.tc_seg_max[b] = (mx + 15) / 16 * 16;
+}
+
+// Tensor-core sweep of one program (complex64, W = 6, 1 or 2 CTAs per
+// vector): the step images are built on the device first, into context
+// scratch that the sweep then reads (stream order keeps consecutive sweeps
+// apart).
+template <int NST, bool VJP>
+static void dispatch_tc(Ctx* ctx, Space* sthis, int CS, const SweepGeom& g0, const RotProgram& rp,
+                        const Mat& X, int nslabs, size_t smem, cudaStream_t st) {
+  SweepGeom g = g0;
+  set_window_geom(g, sthis, tc::kW);
+  Space::Win& wt = sthis->win[tc::kW];
+  build_tc_index(sthis, 0);
+  g.tc_seg_full = wt.tc_seg[0];
+  g.tc_idx_full = wt.tc_idx[0];
+  if (CS > 1) {
+    build_tc_index(sthis, 1);
+    g.tc_seg_grp = wt.tc_seg[1];
+    g.tc_idx_grp = wt.tc_idx[1];
+  }
+  const WProg<double> wpd = make_wprog<double>(rp, sthis->norb, tc::kW);
+  const WProg<float> wpf = make_wprog<float>(rp, sthis->norb, tc::kW);
+  unsigned char* img = (unsigned char*)scratch(
+      ctx, "tc_steps", (size_t)std::max(1, wpd.nsteps) * tc::kStepBytes);
+  if (wpd.nsteps > 0) {
+    ProfScope ps("tc_step_images", st);
+    k_tc_bmats<<<wpd.nsteps, 256, 0, st>>>(wpd, img);
+    FS_CUDA(cudaGetLastError());
+  }
+  g.tc_b = img;
+  if (CS == 1)
+    launch_sweep_t<float, 1, NST, VJP, tc::kW, tc::kThreads, false, WProg<float>, true>(
+        g, wpf, X, nslabs, smem, st);
+  else
+    launch_sweep_t<float, 2, NST, VJP, tc::kW, tc::kThreads, false, WProg<float>, true>(
+        g, wpf, X, nslabs, smem, st);
+}
+
 template <typename R, int NST, bool VJP>
 static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotProgram& rp,
                           const Mat& X, int nslabs, size_t smem, bool two_per_sm,
@@ -1070,6 +1543,7 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
       g.npass = sthis->npass;
     }
   }
+  g.status = ctx->d_status;
   const size_t csz = dtype == FS_C64 ? 8 : 16;
   const size_t maxsm = (size_t)ctx->prop.sharedMemPerBlockOptin;
   const size_t tab_per_kv = ph.has_x ? g.nchunk * 256 * csz : 0;
@@ -1079,6 +1553,49 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
     size_t chunk = (g.d + CS - 1) / CS;
     return (size_t)KV * (chunk * csz * nst + tab_per_kv + fixed) + tsum;
   };
+  // tensor-core window steps: complex64, a window of 6 orbitals, the vector
+  // on 1 CTA or a blocked pair (the step images take 2 x 35 KB)
+  if (dtype == FS_C64 && ctx->sweep_engine == FS_SWEEP_TENSOR && sthis->norb >= tc::kW &&
+      sthis->dim > 1 && ctx->prop.major >= 10) {
+    Space* sw0 = const_cast<Space*>(sthis);
+    build_tc_index(sw0, 0);
+    for (int CS = 1; CS <= 2; CS *= 2) {
+      if (CS > 1) build_tc_index(sw0, 1);
+      const Space::Win& wt = sthis->win[tc::kW];
+      const int cap = CS > 1 ? std::max(wt.tc_seg_max[0], wt.tc_seg_max[1]) : wt.tc_seg_max[0];
+      auto smem_tc = [&](size_t chunk, int KV) {
+        return (size_t)KV * chunk * csz * nst +
+               std::max<size_t>(128 + 2 * (size_t)tc::kStepBytes + 2 * (size_t)cap,
+                                (size_t)KV * (tab_per_kv + fixed) + tsum);
+      };
+      SweepGeom gt = g;
+      gt.tc_idx_cap = cap;
+      set_cluster_layout(gt, sthis, CS, [&](int chunk) { return smem_tc(chunk, 1) <= maxsm; });
+      if (CS > 1 && !gt.blocked) continue;
+      if (smem_tc(gt.chunk, 1) > maxsm) continue;
+      int want = std::max(1, gt.nvec / (2 * ctx->prop.multiProcessorCount));
+      int lg = 0;
+      while ((2 << lg) <= std::min(want, kMaxKV) && smem_tc(gt.chunk, 2 << lg) <= maxsm) ++lg;
+      gt.lgKV = lg;
+      if (gt.blocked && gt.npass > 0) {
+        build_tpass_groups(const_cast<Space*>(sthis), gt.lgcs);
+        gt.trec_grp = sthis->tgrec[gt.lgcs];
+        gt.tgoff = sthis->tgoff[gt.lgcs];
+      }
+      const int KV = 1 << lg;
+      const int nslabs = (gt.nvec + KV - 1) / KV;
+      // more than half an SM's shared memory: one CTA per SM, so that no two
+      // CTAs (of different clusters) ever wait on one SM's tensor memory
+      const size_t smem = std::max(smem_tc(gt.chunk, KV),
+                                   (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 + 1024);
+      Space* sw = const_cast<Space*>(sthis);
+      if (nst == 1)
+        dispatch_tc<1, false>(ctx, sw, CS, gt, rp, ph.X, nslabs, smem, st);
+      else
+        dispatch_tc<2, true>(ctx, sw, CS, gt, rp, ph.X, nslabs, smem, st);
+      return;
+    }
+  }
   int CS = 1;
   while (CS <= 8 && smem_for(CS, 1) > maxsm) CS *= 2;
   FS_REQUIRE(CS <= 8, FS_ERR_UNSUPPORTED, "state vector too large for a cluster of 8");

@@ -20,6 +20,7 @@ from .build import lib_path
 
 FS_C64, FS_C128 = 0, 1
 FS_ROT_AUTO, FS_ROT_GIVENS, FS_ROT_MINORS = 0, 1, 2
+FS_SWEEP_AUTO, FS_SWEEP_CUDA_CORE, FS_SWEEP_TENSOR = 0, 1, 2
 
 STATUS = {0: "FS_OK", -1: "FS_ERR_ARG", -2: "FS_ERR_NOT_UNITARY", -3: "FS_ERR_NOMEM",
           -4: "FS_ERR_CUDA", -5: "FS_ERR_TIMEOUT", -6: "FS_ERR_BOUNDS",
@@ -70,6 +71,8 @@ SIGNATURES = {
     "fs_apply_molecular_hamiltonian": [_P, _P, _P, _I, _P, _P, _D, _I64, _I, _I, _I, _P],
     "fs_sample_state": [_P, _P, _I, _I, _I, _I, _P, _I64, _P, _P],
     "fs_sample_slater": [_P, _P, _I, _P, _I, _P, _I64, _P, _P],
+    "fs_set_sweep_engine": [_P, _I],
+    "fs_measure_fp32_fma": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                       _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
 }
@@ -120,6 +123,14 @@ class Context:
     def set_rotation_path(self, path):
         _check("fs_set_rotation_path", load_library().fs_set_rotation_path(self.handle, int(path)))
 
+    def set_sweep_engine(self, engine):
+        _check("fs_set_sweep_engine", load_library().fs_set_sweep_engine(self.handle, int(engine)))
+
+    def sync_status(self, stream=None):
+        """The device status word (FS_OK, or FS_ERR_TIMEOUT / FS_ERR_BOUNDS
+        from a kernel's bounded checks), reset to FS_OK."""
+        return load_library().fs_sync_status(self.handle, _stream_ptr(stream))
+
     def profile_start(self):
         _check("fs_profile_start", load_library().fs_profile_start(self.handle))
 
@@ -129,9 +140,6 @@ class Context:
         buf = ctypes.create_string_buffer(1 << 16)
         _check("fs_profile_stop", load_library().fs_profile_stop(self.handle, buf, len(buf)))
         return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
-
-    def sync_status(self, stream=None):
-        return load_library().fs_sync_status(self.handle, _stream_ptr(stream))
 
 
 _contexts = {}
@@ -529,3 +537,16 @@ def sample_slater(norb, occ, U, shots=None, uniforms=None, seed=0, device=None, 
     us = uniforms if uniforms is not None else (None, None)
     return tuple(_slater_spin(Us[s], occ[s], norb, shots, us[s], seed + s, device, ctx)
                  for s in range(2))
+
+
+# ------------------------------------------------------------ measurement
+def measure_fp32_fma(device=None):
+    """FP32 FMA throughput of the current (or given) device in TFLOP/s, and
+    the time of one probe launch in ms (library kernel, CUDA events)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    with torch.cuda.device(dev):
+        tf, ms = _D(0), _D(0)
+        _check("fs_measure_fp32_fma", load_library().fs_measure_fp32_fma(
+            _P(torch.cuda.current_stream(dev).cuda_stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value

@@ -30,9 +30,10 @@ def test_element_givens_per_amplitude():
     N, n = 8, 4
     eg = N * (N - 1) / 2 * touched_fraction(N, n, 3)
     flops = bench.algorithmic_flops("sweep_beta_f32", N, (n, n), 1)
-    assert math.isclose(flops, 12 * eg, rel_tol=1e-12)
-    # the N=16 (8,8) figure quoted in the design notes: 64 per amplitude
-    assert math.isclose(bench.algorithmic_flops("sweep_beta_f32", 16, (8, 8), 1), 12 * 64,
+    assert math.isclose(flops, 10 * eg, rel_tol=1e-12)
+    # the N=16 (8,8) figure quoted in the design notes: 64 per amplitude,
+    # 10 real flops each (2 for c x, 6 for the complex product s y, 2 for the sum)
+    assert math.isclose(bench.algorithmic_flops("sweep_beta_f32", 16, (8, 8), 1), 10 * 64,
                         rel_tol=1e-12)
 
 
@@ -45,7 +46,7 @@ def test_reverse_sweep_flops_add_the_transition_reduction():
     # per launch at full size (the benchmark's algorithmic flops)
     amps = math.comb(16, 8) ** 2
     assert math.isclose(bench.algorithmic_flops("sweep_vjp_beta_f32", N, (n, n), amps),
-                        3.498e11, rel_tol=1e-3)
+                        3.074e11, rel_tol=1e-3)
 
 
 def test_bytes_per_launch():
