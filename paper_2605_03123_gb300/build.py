@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libfsgpu.so"
 SOURCES = ["fs_api.cu", "fs_tables.cu", "fs_sweep.cu", "fs_reduce.cu", "fs_minor.cu",
-           "fs_phase_tc.cu", "fs_batch.cu", "fs_operator.cu", "fs_noalloc.cu", "fs_sample.cu", "fs_peak.cu",
+           "fs_phase_tc.cu", "fs_batch.cu", "fs_operator.cu", "fs_noalloc.cu", "fs_sample.cu", "fs_peak.cu", "fs_gemm_tc.cu",
            "fs_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -56,7 +56,7 @@ def build(verbose=False, extra_flags=()):
         objs = list(ex.map(one, srcs))
     out = lib_path()
     tmp = out + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -229,7 +229,7 @@ static void phase_pass(Ctx* ctx, Space* sa, Space* sb, void* vec, int dtype,
     ph.has_x = 1;
     ph.X = real_mat(J_ab, sa->norb, xscale);
   }
-  if (ph.has_x && phase_tc_supported(dtype, sa))
+  if (ph.has_x && phase_tc_supported(dtype, sa, sb, vec))
     launch_phase_tc(ctx, sa, sb, vec, ph, st);
   else
     launch_phase(sa, sb, vec, dtype, ph, st);
@@ -475,7 +475,6 @@ int fs_destroy(fs_ctx* ctx) {
     for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
     cudaFree(ctx->d_status);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-    release_blas(ctx);
     delete ctx;
   });
 }

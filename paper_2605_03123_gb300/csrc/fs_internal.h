@@ -203,7 +203,6 @@ struct Ctx {
   // a graph (a capture cannot run on the legacy default stream); the graph
   // itself is launched on the caller's stream
   cudaStream_t capture_stream = nullptr;
-  void* blas = nullptr;  // cuBLAS handle (operator action), created on first use
   std::mutex mu;
 };
 
@@ -429,7 +428,6 @@ void build_gather_table(Space* sp, cudaStream_t st);
 void molecular_hamiltonian(Ctx* ctx, Space* sa, Space* sb, const void* vec, void* out, int dtype,
                            const double* h1, const double* h2, double constant,
                            int64_t workspace_bytes, cudaStream_t st);
-void release_blas(Ctx* ctx);
 // Configurations drawn from |vec|^2 by inverse CDF in address order, for
 // `shots` device uniforms; n = dim_a * dim_b amplitudes.
 void sample_state(Ctx* ctx, const void* vec, int dtype, int64_t n, const double* u,
@@ -449,7 +447,7 @@ void launch_phase(const Space* sa, const Space* sb, void* vec, int dtype,
                   const PhaseDev& ph, cudaStream_t st);
 // The same pass with the cross term contracted on the tensor cores
 // (complex64, norb <= 32; needs scratch for the per-column angle table).
-bool phase_tc_supported(int dtype, const Space* sa);
+bool phase_tc_supported(int dtype, const Space* sa, const Space* sb, const void* vec);
 void launch_phase_tc(Ctx* ctx, const Space* sa, const Space* sb, void* vec, const PhaseDev& ph,
                      cudaStream_t st);
 
@@ -467,6 +465,36 @@ void launch_minor_rotation(Ctx* ctx, const Space* sa, const Space* sb, void* vec
                            const CMat& Ua, const CMat& Ub, cudaStream_t st);
 // masks[dim] of the strings of nocc electrons in norb orbitals, into `out`.
 void launch_masks(uint32_t* out, int norb, int nocc, cudaStream_t st);
+// ------------------------------------------------ tensor-core GEMM
+// C[m][n] = sum_k A[m][k] B[n][k] on the tcgen05 tensor cores with both
+// operands as three exact BF16 pieces (K contiguous, rows a multiple of 16
+// bytes apart), FP32 accuracy (fs_gemm_tc.cu).  Output forms:
+//   GEMM_REAL:          float out[m * ldo + n];
+//   GEMM_REAL_T:        float out[n * ldo + m];
+//   GEMM_CPLX_T:        N even, (C[m][2j], C[m][2j+1]) is the complex
+//                       float2 out[j * ldo + m];
+//   GEMM_CPLX_T_PLANES: as GEMM_CPLX_T, written as the three BF16 planes
+//                       outp[p] (row j, columns 2m, 2m + 1; row stride ldp).
+enum { GEMM_REAL = 0, GEMM_REAL_T = 1, GEMM_CPLX_T = 2, GEMM_CPLX_T_PLANES = 3 };
+struct GemmTc {
+  const uint16_t* A[3];
+  const uint16_t* B[3];
+  int M, N, K;
+  int64_t lda, ldb;
+  void* out;
+  int mode;
+  int64_t ldo;
+  void* outp[3];
+  int64_t ldp;
+  int* status;
+};
+void gemm_tc(const GemmTc& g, cudaStream_t st);
+// The three BF16 planes of a complex matrix X (rows x cols, leading
+// dimension ldx complex) with row stride ldk (>= 2 cols, a multiple of 8;
+// the padding is zeroed).
+void split_planes(const void* X, int64_t rows, int cols, int64_t ldx, void* const planes[3],
+                  int64_t ldk, cudaStream_t st);
+
 // Force the module loads of the kernels the allocation-free entry point
 // launches (k_masks; k_string_phase and k_phase in both precisions), so
 // that none of them loads lazily on a later call.

@@ -4,8 +4,12 @@
 // operator of |I> = cre(I)|vac>, the rotated string is
 //   U|I> = sum_J det(U[J, I]) |J>   (rows J, columns I, both ascending),
 // so one spin is rotated by the matrix M[J][I] = det(U[J, I]) and the state
-// by psi' = M_a psi M_b^T.  The minors are computed in FP64 on the device,
-// then the two products run as tiled complex GEMMs in the state precision.
+// by psi' = M_a psi M_b^T.  The minors are computed in FP64 on the device.
+// complex64: the two products run on the tcgen05 tensor cores (gemm_tc,
+// operands as exact BF16 triples, FP32 accuracy), the complex matrices in
+// real form; complex128: tiled complex GEMMs on the FP64 CUDA cores.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "fs_common.cuh"
@@ -132,6 +136,143 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The minor matrix M[J][I] = det(U[J, I]) in the real form of a complex
+// right operand, as three BF16 planes (row stride ld): row 2J + x, column
+// 2I + y holds [[Re, -Im], [Im, Re]][x][y] of M[J][I], split from FP64 into
+// the nearest BF16 of each remainder.  One thread per (J, I).
+__global__ void k_minor_planes(const uint32_t* masks, int64_t d, int norb, int n,
+                               const __grid_constant__ CMat U, __nv_bfloat16* p0,
+                               __nv_bfloat16* p1, __nv_bfloat16* p2, int64_t ld) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= d * d) return;
+  const int64_t J = t / d, I = t - J * d;
+  double2 a[kMinorMaxN * kMinorMaxN];
+  const uint32_t mj = masks[J], mi = masks[I];
+  int r = 0;
+  for (int p = 0; p < norb; ++p) {
+    if (!((mj >> p) & 1u)) continue;
+    int c = 0;
+    for (int q = 0; q < norb; ++q) {
+      if (!((mi >> q) & 1u)) continue;
+      a[r * n + c] = make_double2(U.v[2 * (p * norb + q)], U.v[2 * (p * norb + q) + 1]);
+      ++c;
+    }
+    ++r;
+  }
+  double dr = 1, di = 0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = hypot(a[k * n + k].x, a[k * n + k].y);
+    for (int i = k + 1; i < n; ++i) {
+      const double h = hypot(a[i * n + k].x, a[i * n + k].y);
+      if (h > best) {
+        best = h;
+        piv = i;
+      }
+    }
+    if (best == 0) {
+      dr = di = 0;
+      break;
+    }
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) {
+        const double2 tmp = a[k * n + c];
+        a[k * n + c] = a[piv * n + c];
+        a[piv * n + c] = tmp;
+      }
+      dr = -dr;
+      di = -di;
+    }
+    const double2 pk = a[k * n + k];
+    const double nr = dr * pk.x - di * pk.y;
+    di = dr * pk.y + di * pk.x;
+    dr = nr;
+    const double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
+    for (int i = k + 1; i < n; ++i) {
+      const double2 x = a[i * n + k];
+      const double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
+      for (int c = k + 1; c < n; ++c) {
+        const double2 y = a[k * n + c];
+        a[i * n + c].x -= fr * y.x - fi * y.y;
+        a[i * n + c].y -= fr * y.y + fi * y.x;
+      }
+    }
+  }
+  const double ent[4] = {dr, -di, di, dr};
+  __nv_bfloat16* planes[3] = {p0, p1, p2};
+  for (int e = 0; e < 4; ++e) {
+    const int64_t off = (2 * J + (e >> 1)) * ld + 2 * I + (e & 1);
+    double rem = ent[e];
+    for (int pc = 0; pc < 3; ++pc) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)rem);
+      planes[pc][off] = b;
+      rem -= (double)__bfloat162float(b);
+    }
+  }
+}
+
+// complex64 on the tensor cores: tmp^T = (psi M_b^T)^T, then
+// psi' = (tmp^T M_a^T)^T, each a real-form GEMM whose right operand is an
+// expanded minor matrix.
+static void minor_rotation_tc(Ctx* ctx, const Space* sa, const Space* sb, void* vec,
+                              const CMat& Ua, const CMat& Ub, cudaStream_t st) {
+  const int64_t da = sa->dim, db = sb->dim;
+  const int64_t lka = (2 * da + 7) / 8 * 8, lkb = (2 * db + 7) / 8 * 8;
+  const size_t pa = (size_t)2 * da * lka, pb = (size_t)2 * db * lkb;  // elements per plane
+  const size_t ppsi = (size_t)da * lkb, ptmp = (size_t)db * lka;
+  uint16_t* Ba = (uint16_t*)scratch(ctx, "minor_tc_a", 3 * pa * 2);
+  uint16_t* Bb = (uint16_t*)scratch(ctx, "minor_tc_b", 3 * pb * 2);
+  uint16_t* Ap = (uint16_t*)scratch(ctx, "minor_tc_psi", 3 * ppsi * 2);
+  uint16_t* Tp = (uint16_t*)scratch(ctx, "minor_tc_tmp", 3 * ptmp * 2);
+  {
+    ProfScope ps("minor_matrices", st, 2);
+    FS_CUDA(cudaMemsetAsync(Ba, 0, 3 * pa * 2, st));
+    FS_CUDA(cudaMemsetAsync(Bb, 0, 3 * pb * 2, st));
+    FS_CUDA(cudaMemsetAsync(Tp, 0, 3 * ptmp * 2, st));
+    k_minor_planes<<<(unsigned)((da * da + 127) / 128), 128, 0, st>>>(
+        sa->masks, da, sa->norb, sa->nocc, Ua, (__nv_bfloat16*)Ba, (__nv_bfloat16*)(Ba + pa),
+        (__nv_bfloat16*)(Ba + 2 * pa), lka);
+    FS_CUDA(cudaGetLastError());
+    k_minor_planes<<<(unsigned)((db * db + 127) / 128), 128, 0, st>>>(
+        sb->masks, db, sb->norb, sb->nocc, Ub, (__nv_bfloat16*)Bb, (__nv_bfloat16*)(Bb + pb),
+        (__nv_bfloat16*)(Bb + 2 * pb), lkb);
+    FS_CUDA(cudaGetLastError());
+  }
+  ProfScope ps("minor_gemm_tc", st, 3);
+  void* psi_planes[3] = {Ap, Ap + ppsi, Ap + 2 * ppsi};
+  split_planes(vec, da, (int)db, db, psi_planes, lkb, st);
+  GemmTc g{};
+  for (int p = 0; p < 3; ++p) {
+    g.A[p] = Ap + p * ppsi;
+    g.B[p] = Bb + p * pb;
+    g.outp[p] = Tp + p * ptmp;
+  }
+  g.M = (int)da;
+  g.N = (int)(2 * db);
+  g.K = (int)(2 * db);
+  g.lda = lkb;
+  g.ldb = lkb;
+  g.mode = GEMM_CPLX_T_PLANES;
+  g.ldp = lka;
+  g.status = ctx->d_status;
+  gemm_tc(g, st);
+  GemmTc h{};
+  for (int p = 0; p < 3; ++p) {
+    h.A[p] = Tp + p * ptmp;
+    h.B[p] = Ba + p * pa;
+  }
+  h.M = (int)db;
+  h.N = (int)(2 * da);
+  h.K = (int)(2 * da);
+  h.lda = lka;
+  h.ldb = lka;
+  h.out = vec;
+  h.mode = GEMM_CPLX_T;
+  h.ldo = db;
+  h.status = ctx->d_status;
+  gemm_tc(h, st);
+}
+
 template <typename R>
 static void minor_rotation_t(Ctx* ctx, const Space* sa, const Space* sb, void* vec,
                              const CMat& Ua, const CMat& Ub, cudaStream_t st) {
@@ -169,7 +310,7 @@ void launch_minor_rotation(Ctx* ctx, const Space* sa, const Space* sb, void* vec
              "the minor-matrix rotation supports string dimensions up to 4096 and at most "
              "16 electrons per spin");
   if (dtype == FS_C64)
-    minor_rotation_t<float>(ctx, sa, sb, vec, Ua, Ub, st);
+    minor_rotation_tc(ctx, sa, sb, vec, Ua, Ub, st);
   else
     minor_rotation_t<double>(ctx, sa, sb, vec, Ua, Ub, st);
 }

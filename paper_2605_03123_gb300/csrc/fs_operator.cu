@@ -9,19 +9,21 @@
 //         + sum_pq E^b_pq [sum_rs V_pqrs E^b_rs],
 //   k_pq = h_pq - 1/2 sum_r h_prrq,  V = h / 2,  W_pqrs = (h_pqrs + h_rspq) / 2.
 // Each bracket is a contraction over rs: with D_rs = E_rs psi it is the
-// plain GEMM G = V D (cuBLAS; complex64 with FP32 emulated on the bf16
-// tensor cores, complex128 in FP64; real matrix times the complex vectors
-// viewed as pairs of reals), and the outer E_pq is a
+// GEMM G = V D (a real matrix times the complex vectors viewed as pairs of
+// reals): complex64 on the tcgen05 tensor cores (gemm_tc: D transposed and
+// split into exact BF16 triples, V split on the host; FP32 accuracy),
+// complex128 as a tiled FP64 GEMM on the CUDA cores; and the outer E_pq is a
 // gather through the single-excitation table.  The beta part runs on
 // blocks of rows (a beta excitation stays in its row), the alpha and mixed
 // parts on blocks of columns (an alpha excitation stays in its column);
 // the block size bounds the N^2 x block intermediates.
-#include <cublas_v2.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
 #include "fs_common.cuh"
 #include "fs_internal.h"
+#include "fs_tc.cuh"
 
 namespace fs {
 
@@ -142,47 +144,119 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-static cublasHandle_t blas_handle(Ctx* ctx) {
-  if (!ctx->blas) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-      set_error("cublasCreate failed");
-      throw Fail{FS_ERR_CUDA};
+// The left operand of the tensor-core contraction: A_q[(2 p + c) * lda + k]
+// = piece q of component c (0 = Re, 1 = Im) of D[k][p], for k < K rows of D
+// (K x X complex, row stride X) and positions p < X; columns K .. lda - 1
+// are zeroed.  32 x 32 tiles through shared memory, so both the reads of D
+// and the writes of the planes run along contiguous memory.
+__global__ void __launch_bounds__(256)
+    k_transpose_split(const float2* D, int K, int64_t X, __nv_bfloat16* A0, __nv_bfloat16* A1,
+                      __nv_bfloat16* A2, int64_t lda) {
+  __shared__ float2 tile[32][33];
+  const int64_t p0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r;
+    const int64_t p = p0 + tx;
+    tile[r][tx] = (k < K && p < X) ? D[(int64_t)k * X + p] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  __nv_bfloat16* planes[3] = {A0, A1, A2};
+  for (int r = ty; r < 32; r += 8) {  // r: position within the tile; tx: k
+    const int64_t p = p0 + r;
+    const int k = k0 + tx;
+    if (p >= X || k >= (int)lda) continue;
+    const float2 v = tile[tx][r];
+    uint32_t w[3];
+    tc::split_bf16x3(v.x, v.y, w[0], w[1], w[2]);  // low half Re, high half Im
+    for (int q = 0; q < 3; ++q) {
+      planes[q][(2 * p) * lda + k] = __ushort_as_bfloat16((unsigned short)(w[q] & 0xFFFFu));
+      planes[q][(2 * p + 1) * lda + k] = __ushort_as_bfloat16((unsigned short)(w[q] >> 16));
     }
-    ctx->blas = h;
   }
-  return (cublasHandle_t)ctx->blas;
 }
 
-void release_blas(Ctx* ctx) {
-  if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
-  ctx->blas = nullptr;
+// G[m][n] = sum_k V[m][k] D[k][n], real FP64 (row-major, leading dimensions
+// ldv, ldd, ldg): 64 x 64 tiles, 256 threads, 4 x 4 outputs per thread.
+constexpr int kRT = 64, kRK = 16;
+__global__ void __launch_bounds__(256)
+    k_rgemm_f64(const double* V, int64_t ldv, const double* D, int64_t ldd, double* G,
+                int64_t ldg, int M, int64_t N, int K) {
+  __shared__ double sa[kRK][kRT + 1];
+  __shared__ double sb[kRK][kRT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kRT;
+  const int64_t n0 = (int64_t)blockIdx.x * kRT;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kRK) {
+    for (int e = threadIdx.x; e < kRK * kRT; e += 256) {
+      const int kk = e / kRT, mm = e - kk * kRT;
+      const int gk = k0 + kk;
+      sa[kk][mm] = (m0 + mm < M && gk < K) ? V[(int64_t)(m0 + mm) * ldv + gk] : 0.0;
+      sb[kk][mm] = (n0 + mm < N && gk < K) ? D[(int64_t)gk * ldd + n0 + mm] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kRK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sa[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sb[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + ty * 4 + i;
+      const int64_t n = n0 + tx * 4 + j;
+      if (m < M && n < N) G[(int64_t)m * ldg + n] = acc[i][j];
+    }
 }
 
-// G (row-major [n][m]) = V (row-major [n][k], leading dimension ldv) x
-// D (row-major [k][m]), real; m counts reals (two per complex element).
-static void gemm(Ctx* ctx, int dtype, int64_t m, int n, int k, const void* D, const void* V,
-                 int ldv, void* G, cudaStream_t st) {
-  FS_REQUIRE(m <= 0x7FFFFFFF, FS_ERR_UNSUPPORTED, "operator block too large for one GEMM");
-  cublasHandle_t h = blas_handle(ctx);
-  cublasSetStream(h, st);
-  cublasStatus_t s;
-  if (dtype == FS_C64) {
-    // FP32 products emulated on the bf16 tensor cores (three-way bf16
-    // splits; FP32-level accuracy): measured 1.25x faster than FP32 FFMA
-    cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH);
-    const float one = 1, zero = 0;
-    s = cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, n, k, &one, (const float*)D, (int)m,
-                    (const float*)V, ldv, &zero, (float*)G, (int)m);
+// G (row-major [n][2X] reals) = V (row-major [n][k] reals, leading dimension
+// ldv; for complex64 its three BF16 planes Vp with the same layout) x
+// D (k rows of X complex).  Ap: scratch for the transposed planes of D.
+template <typename R>
+static void contract(Ctx* ctx, int64_t X, int n, int k, const void* D, const R* Vd,
+                     const uint16_t* Vp, int ldv, int ldvp, void* G, uint16_t* Ap,
+                     cudaStream_t st) {
+  FS_REQUIRE(2 * X <= 0x7FFFFFFF, FS_ERR_UNSUPPORTED, "operator block too large for one GEMM");
+  if constexpr (sizeof(R) == 4) {
+    const int64_t lda = (k + 7) / 8 * 8;
+    const size_t plane = (size_t)2 * X * lda;
+    dim3 grid((unsigned)((X + 31) / 32), (unsigned)((lda + 31) / 32));
+    k_transpose_split<<<grid, 256, 0, st>>>((const float2*)D, k, X, (__nv_bfloat16*)Ap,
+                                            (__nv_bfloat16*)(Ap + plane),
+                                            (__nv_bfloat16*)(Ap + 2 * plane), lda);
+    FS_CUDA(cudaGetLastError());
+    GemmTc g{};
+    for (int q = 0; q < 3; ++q) {
+      g.A[q] = Ap + q * plane;
+      g.B[q] = Vp + (size_t)q * n * ldvp;
+    }
+    g.M = (int)(2 * X);
+    g.N = n;
+    g.K = k;
+    g.lda = lda;
+    g.ldb = ldvp;
+    g.out = G;
+    g.mode = GEMM_REAL_T;
+    g.ldo = 2 * X;
+    g.status = ctx->d_status;
+    gemm_tc(g, st);
   } else {
-    cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
-    const double one = 1, zero = 0;
-    s = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)m, n, k, &one, (const double*)D, (int)m,
-                    (const double*)V, ldv, &zero, (double*)G, (int)m);
-  }
-  if (s != CUBLAS_STATUS_SUCCESS) {
-    set_error("cuBLAS GEMM failed with status " + std::to_string((int)s));
-    throw Fail{FS_ERR_CUDA};
+    dim3 grid((unsigned)((2 * X + kRT - 1) / kRT), (unsigned)((n + kRT - 1) / kRT));
+    k_rgemm_f64<<<grid, 256, 0, st>>>(Vd, ldv, (const double*)D, 2 * X, (double*)G, 2 * X, n,
+                                      2 * X, k);
+    FS_CUDA(cudaGetLastError());
   }
 }
 
@@ -192,7 +266,6 @@ static void molecular_hamiltonian_t(Ctx* ctx, Space* sa, Space* sb, const void* 
                                     int64_t ws, cudaStream_t st) {
   using C = cx_t<R>;
   const int N = sa->norb, NN = N * N;
-  const int dtype = sizeof(R) == 4 ? FS_C64 : FS_C128;
   const C* vec = (const C*)vec_;
   C* out = (C*)out_;
   const int64_t da = sa->dim, db = sb->dim;
@@ -215,6 +288,28 @@ static void molecular_hamiltonian_t(Ctx* ctx, Space* sa, Space* sb, const void* 
     }
   R* Vd = (R*)scratch(ctx, "op_V", V.size() * sizeof(R));
   FS_CUDA(cudaMemcpyAsync(Vd, V.data(), V.size() * sizeof(R), cudaMemcpyHostToDevice, st));
+  uint16_t* Vp = nullptr;
+  std::vector<uint16_t> Vh;
+  const int ldvp = (2 * NN + 7) / 8 * 8;
+  if (sizeof(R) == 4) {
+    // three BF16 planes of V from FP64 (each the nearest BF16 of the
+    // remainder), rows padded to a multiple of 8 entries (16 bytes)
+    const size_t nv = (size_t)NN * ldvp;
+    Vh.assign(3 * nv, 0);
+    for (int pq = 0; pq < NN; ++pq)
+      for (int rs = 0; rs < 2 * NN; ++rs) {
+        const double a = h2[(size_t)pq * NN + rs % NN], b = h2[(size_t)(rs % NN) * NN + pq];
+        double r = rs < NN ? 0.5 * a : 0.5 * (a + b);
+        for (int q = 0; q < 3; ++q) {
+          const __nv_bfloat16 v = __float2bfloat16_rn((float)r);
+          Vh[q * nv + (size_t)pq * ldvp + rs] = __bfloat16_as_ushort(v);
+          r -= (double)__bfloat162float(v);
+        }
+      }
+    Vp = (uint16_t*)scratch(ctx, "op_Vp", Vh.size() * sizeof(uint16_t));
+    FS_CUDA(cudaMemcpyAsync(Vp, Vh.data(), Vh.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                            st));
+  }
   // block sizes from the workspace budget (D and G together)
   const size_t csz = sizeof(C);
   size_t budget = (size_t)ws;
@@ -223,11 +318,17 @@ static void molecular_hamiltonian_t(Ctx* ctx, Space* sa, Space* sb, const void* 
     FS_CUDA(cudaMemGetInfo(&fr, &tot));
     budget = std::min<size_t>((size_t)8 << 30, fr / 4);
   }
-  const int64_t nr = std::max<int64_t>(1, std::min<int64_t>(da, budget / (2 * NN * csz * db)));
-  const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(db, budget / (3 * NN * csz * da)));
+  // per position: D (2 N^2 complex), G (N^2 complex) and, for complex64, the
+  // transposed BF16 planes of D (3 x 2 x 2 N^2 x 2 bytes)
+  const size_t per = (size_t)3 * NN * csz + (sizeof(R) == 4 ? (size_t)24 * NN : 0);
+  const int64_t nr = std::max<int64_t>(1, std::min<int64_t>(da, budget / (per * db)));
+  const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(db, budget / (per * da)));
   const int64_t xmax = std::max(nr * db, nc * da);
   C* D = (C*)scratch(ctx, "op_D", (size_t)2 * NN * xmax * csz);
   C* G = (C*)scratch(ctx, "op_G", (size_t)NN * xmax * csz);
+  uint16_t* Ap = sizeof(R) == 4
+                     ? (uint16_t*)scratch(ctx, "op_Dp", (size_t)3 * 2 * xmax * (2 * NN + 8) * 2)
+                     : nullptr;
   const int sms = ctx->prop.multiProcessorCount;
   // beta part on row blocks; also writes c psi and the beta one-body term
   for (int64_t i0 = 0; i0 < da; i0 += nr) {
@@ -240,8 +341,8 @@ static void molecular_hamiltonian_t(Ctx* ctx, Space* sa, Space* sb, const void* 
       FS_CUDA(cudaGetLastError());
     }
     {
-      ProfScope ps("op_gemm", st, 0);
-      gemm(ctx, dtype, 2 * X, NN, NN, D, Vd, 2 * NN, G, st);
+      ProfScope ps("op_gemm", st, sizeof(R) == 4 ? 2 : 1);
+      contract<R>(ctx, X, NN, NN, D, Vd, Vp, 2 * NN, ldvp, G, Ap, st);
     }
     {
       ProfScope ps("op_gather", st);
@@ -266,8 +367,8 @@ static void molecular_hamiltonian_t(Ctx* ctx, Space* sa, Space* sb, const void* 
       FS_CUDA(cudaGetLastError());
     }
     {
-      ProfScope ps("op_gemm", st, 0);
-      gemm(ctx, dtype, 2 * X, NN, 2 * NN, D, Vd, 2 * NN, G, st);
+      ProfScope ps("op_gemm", st, sizeof(R) == 4 ? 2 : 1);
+      contract<R>(ctx, X, NN, 2 * NN, D, Vd, Vp, 2 * NN, ldvp, G, Ap, st);
     }
     {
       ProfScope ps("op_gather", st);

@@ -1696,11 +1696,12 @@ void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* 
   g.cb[1] = g.d;
   out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
   out.smem = smem_for(1 << lg);
-  out.prog.resize(wprog_bytes(dtype));
   if (dtype == FS_C64) {
+    out.prog.resize(wprog_bytes(dtype));
     auto w = make_wprog<float>(rp, sthis->norb, W);
     memcpy(out.prog.data(), &w, sizeof(w));
   } else {
+    out.prog.resize(wprog_bytes(dtype));
     auto w = make_wprog<double>(rp, sthis->norb, W);
     memcpy(out.prog.data(), &w, sizeof(w));
   }
