@@ -199,12 +199,19 @@ def run_gpu(args):
     fsgpu.load_library()
     ctx = fsgpu.context(local)
     global NORB, NELEC, NLAYERS, WORKLOAD
-    w = workload(args)
     if args.norb:
         NORB, NELEC, NLAYERS = args.norb, (args.nalpha, args.nbeta), args.layers
         WORKLOAD = "lucj_fwd_vjp_norb%d_nelec%d_%d_%dlayers" % (NORB, NELEC[0], NELEC[1], NLAYERS)
-    K, Jaa, Jab = w["K"], w["J_aa"], w["J_ab"]
     da, db = math.comb(NORB, NELEC[0]), math.comb(NORB, NELEC[1])
+    # pinned host buffers of the end-to-end leg, allocated before the
+    # multi-GB host workload arrays exist (pinned pages placed later copied
+    # at a fraction of the link rate on the GB300 host)
+    if args.e2e_steps > 0:
+        hv = torch.empty((da, db), dtype=torch.complex64, pin_memory=True)
+        hc = torch.empty((da, db), dtype=torch.complex64, pin_memory=True)
+        hout = torch.empty((da, db), dtype=torch.complex64, pin_memory=True)
+    w = workload(args)
+    K, Jaa, Jab = w["K"], w["J_aa"], w["J_ab"]
     S = 8 * da * db
     vec0 = torch.from_numpy(w["vec"].astype(np.complex64)).cuda()
     cot0 = torch.from_numpy(w["cot"].astype(np.complex64)).cuda()
@@ -252,9 +259,8 @@ def run_gpu(args):
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        hv = torch.from_numpy(w["vec"].astype(np.complex64)).pin_memory()
-        hc = torch.from_numpy(w["cot"].astype(np.complex64)).pin_memory()
-        hout = torch.empty_like(hc).pin_memory()
+        hv.copy_(torch.from_numpy(w["vec"].astype(np.complex64)))
+        hc.copy_(torch.from_numpy(w["cot"].astype(np.complex64)))
         dv, dc = torch.empty_like(vec0), torch.empty_like(cot0)
         side = torch.cuda.Stream()
         main = torch.cuda.current_stream()
@@ -580,9 +586,9 @@ def run_largest(args, ctx):
 
 def run_dc_phase(args, ctx):
     """Standalone diagonal-Coulomb evolution at N=16 (8,8): one streaming
-    pass over the state (algorithmic bytes 2S).  complex64 takes the
-    tensor-core cross term (mma.sync bf16 pieces), complex128 the CUDA-core
-    subset-sum tables."""
+    pass over the state (algorithmic bytes 2S) after the per-string tables.
+    complex64 takes the TMA / tcgen05 pass (cross term on the tensor cores),
+    complex128 the CUDA-core subset-sum tables."""
     import torch
     from paper_2605_03123_gb300 import fsgpu, inputs
     peak, kind = peaks()
@@ -596,10 +602,18 @@ def run_dc_phase(args, ctx):
         f = lambda: fsgpu.apply_diag_coulomb_evolution_(v, Ja, Jb, 0.3, 16, (8, 8), ctx=ctx)
         for _ in range(3):
             f()
+        ctx.profile_start()
         ms = _timed(lambda: [f() for _ in range(5)]) / 5
+        prof = ctx.profile_stop()
         gbs = 2 * S / (ms / 1e3) / 1e9
         out[name] = {"ms": ms, "algorithmic_bytes": 2 * S, "achieved_gbs": gbs,
-                     "frac": gbs / peak}
+                     "frac": gbs / peak,
+                     "kernels_ms": {k: v_[1] / max(1, v_[0]) for k, v_ in prof.items()}}
+        # the streaming pass alone (complex64: the TMA / tcgen05 kernel)
+        if "phase_tc_f32" in prof:
+            kms = prof["phase_tc_f32"][1] / max(1, prof["phase_tc_f32"][0])
+            out[name]["stream_kernel_ms"] = kms
+            out[name]["stream_kernel_frac"] = 2 * S / (kms / 1e3) / 1e9 / peak
         del v
     torch.cuda.empty_cache()
     return out

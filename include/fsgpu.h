@@ -119,6 +119,21 @@ int fs_set_rotation_path(fs_ctx *ctx, int path);
 enum { FS_SWEEP_AUTO = 0, FS_SWEEP_CUDA_CORE = 1, FS_SWEEP_TENSOR = 2 };
 int fs_set_sweep_engine(fs_ctx *ctx, int engine);
 
+/* Autotuner of the batched LUCJ sweeps (fs_lucj_batch): on the first call
+ * that meets a sector (norb, electrons of both spins), precision and sweep
+ * kind, every slab width (vectors per CTA, 1 .. 64 within the stage's
+ * shared-memory budget) is timed as a one-circuit launch of the batched
+ * kernel on scratch states, before the batch is captured, and the fastest
+ * is kept for the context.  on = 0 switches it off (and forgets the choices;
+ * untuned batches use about eight slabs per circuit); on = 1 (the default)
+ * switches it on.  Not part of the paper's method: a scheduling aid. */
+int fs_set_batch_tuning(fs_ctx *ctx, int on);
+/* The autotuner's choices as JSON, NUL terminated, into out[0..cap):
+ * [{"norb", "n_this", "n_other", "dtype", "states", "reverse", "cross",
+ *   "budget_kb", "vectors_per_cta", "ms": [per slab width 1, 2, 4, ...]}].
+ * FS_ERR_ARG if it does not fit. */
+int fs_tuning_report(fs_ctx *ctx, char *out, int64_t cap);
+
 /* Measures the device's FP32 fused multiply-add throughput (the denominator
  * of the arithmetic roofline of the Givens sweeps): 8 blocks of 256 threads
  * per SM, each thread running 8 independent FMA chains, timed with CUDA

@@ -475,6 +475,7 @@ int fs_destroy(fs_ctx* ctx) {
     for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
     cudaFree(ctx->d_status);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->tune_stream) cudaStreamDestroy(ctx->tune_stream);
     delete ctx;
   });
 }
@@ -557,6 +558,43 @@ int fs_set_sweep_engine(fs_ctx* ctx, int engine) {
     FS_REQUIRE(engine >= FS_SWEEP_AUTO && engine <= FS_SWEEP_TENSOR, FS_ERR_ARG,
                "unknown sweep engine");
     ctx->sweep_engine = engine;
+  });
+}
+
+int fs_set_batch_tuning(fs_ctx* ctx, int on) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr, FS_ERR_ARG, "null context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->batch_tuning = on ? 1 : 0;
+    if (!on) {
+      ctx->sweep_tune.clear();
+      ctx->sweep_tune_ms.clear();
+    }
+  });
+}
+
+int fs_tuning_report(fs_ctx* ctx, char* out, int64_t cap) {
+  return guarded([&] {
+    FS_REQUIRE(ctx != nullptr && out != nullptr && cap > 0, FS_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::string js = "[";
+    for (const auto& kv : ctx->sweep_tune) {
+      const auto& k = kv.first;
+      if (js.size() > 1) js += ",";
+      js += "{\"norb\":" + std::to_string(k[0]) + ",\"n_this\":" + std::to_string(k[1]) +
+            ",\"n_other\":" + std::to_string(k[2]) + ",\"dtype\":" + std::to_string(k[3]) +
+            ",\"states\":" + std::to_string(k[4]) + ",\"reverse\":" + std::to_string(k[5]) +
+            ",\"cross\":" + std::to_string(k[6]) + ",\"budget_kb\":" + std::to_string(k[7]) +
+            ",\"vectors_per_cta\":" + std::to_string(1 << kv.second) + ",\"ms\":[";
+      const auto m = ctx->sweep_tune_ms.find(k);
+      if (m != ctx->sweep_tune_ms.end())
+        for (size_t i = 0; i < m->second.size(); ++i)
+          js += (i ? "," : "") + std::to_string(m->second[i]);
+      js += "]}";
+    }
+    js += "]";
+    FS_REQUIRE((int64_t)js.size() < cap, FS_ERR_ARG, "report buffer too small");
+    memcpy(out, js.c_str(), js.size() + 1);
   });
 }
 

@@ -9,14 +9,14 @@
 // six products A_i B_j with i + j <= 4 over the pieces are accumulated in
 // TMEM (FP32); the dropped products are below 2^-24 of the result.
 //
-// A CTA computes a 128 x 128 tile of C: K is walked in chunks of 32, each
-// chunk's six piece-tiles (A1..A3, B1..B3, 8 KB each) copied by cp.async
-// into a four-stage shared-memory ring in the K-major no-swizzle
+// A CTA computes a 128 x 256 tile of C: K is walked in chunks of 32, each
+// chunk's six piece-tiles (A1..A3: 8 KB each, B1..B3: 16 KB each) copied by
+// cp.async into a three-stage shared-memory ring in the K-major no-swizzle
 // core-matrix layout (8 rows x 16 bytes per core matrix, LBO = 128 B along
 // K, SBO = 512 B between 8-row groups); one thread issues the 12 MMAs of a
-// chunk (128 x 128 x 16 each) and commits them to the stage's mbarrier,
-// which frees the stage for the chunk three ahead.  The epilogue reads the
-// tile from TMEM (warp w: lanes 32 (w mod 4), columns 64 (w / 4) ..) and
+// chunk (128 x 256 x 16 each) and commits them to the stage's mbarrier,
+// which frees the stage for the chunk two ahead.  The epilogue reads the
+// tile from TMEM (warp w: lanes 32 (w mod 4), columns 128 (w / 4) ..) and
 // writes it in one of the output forms below.  Waits are bounded (status
 // word FS_ERR_TIMEOUT on give-up); the TMEM is always freed.
 #include <cuda_bf16.h>
@@ -30,14 +30,15 @@
 namespace fs {
 namespace gtc {
 
-constexpr int BM = 128, BN = 128, BK = 32, STAGES = 4, THREADS = 256;
-constexpr int TILE_BYTES = BM * BK * 2;      // one BF16 piece of A or B: 8 KB
-constexpr int STAGE_BYTES = 6 * TILE_BYTES;  // A1 A2 A3 B1 B2 B3
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3, THREADS = 256;
+constexpr int A_BYTES = BM * BK * 2;         // one BF16 piece of A: 8 KB
+constexpr int B_BYTES = BN * BK * 2;         // one BF16 piece of B: 16 KB
+constexpr int STAGE_BYTES = 3 * A_BYTES + 3 * B_BYTES;
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
 constexpr uint32_t SBO = (BK / 8) * 128;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
-static_assert(BM == BN, "one tile size for both operands");
+constexpr int A_CHUNKS = BM * BK / 8, B_CHUNKS = BN * BK / 8;  // 16-byte copies per piece
 
 }  // namespace gtc
 
@@ -66,18 +67,22 @@ __global__ void __launch_bounds__(gtc::THREADS, 1) k_gemm_tc(const __grid_consta
   auto load = [&](int kc, int s) {
     const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
     const int k0 = kc * BK;
-    for (int c = tid; c < 6 * 512; c += THREADS) {
-      const int piece = c >> 9, cc = c & 511;
+    for (int c = tid; c < 3 * (A_CHUNKS + B_CHUNKS); c += THREADS) {
+      const bool isA = c < 3 * A_CHUNKS;
+      const int cb = isA ? c : c - 3 * A_CHUNKS;
+      const int piece = isA ? cb / A_CHUNKS : cb / B_CHUNKS;
+      const int cc = isA ? cb - piece * A_CHUNKS : cb - piece * B_CHUNKS;
       const int r = ((cc >> 5) << 3) | (cc & 7), kq = (cc >> 3) & 3;
-      const bool isA = piece < 3;
       const int row = (isA ? m0 : n0) + r;
-      const uint16_t* src = isA ? g.A[piece] : g.B[piece - 3];
+      const uint16_t* src = isA ? g.A[piece] : g.B[piece];
       const int64_t ld = isA ? g.lda : g.ldb;
       const int kk = k0 + kq * 8;
       int bytes = 0;
       if (row < (isA ? g.M : g.N) && kk < g.K) bytes = min(8, g.K - kk) * 2;
       const uint16_t* gp = bytes ? src + (int64_t)row * ld + kk : src;
-      const uint32_t dst = st + (uint32_t)(piece * TILE_BYTES) + (uint32_t)((r >> 3) * SBO) +
+      const uint32_t base = isA ? (uint32_t)(piece * A_BYTES)
+                                : (uint32_t)(3 * A_BYTES + piece * B_BYTES);
+      const uint32_t dst = st + base + (uint32_t)((r >> 3) * SBO) +
                            (uint32_t)(kq * 128 + (r & 7) * 16);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gp),
                    "r"(bytes)
@@ -102,8 +107,8 @@ __global__ void __launch_bounds__(gtc::THREADS, 1) k_gemm_tc(const __grid_consta
       for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
         for (int ks = 0; ks < BK / 16; ++ks) {
-          const uint64_t ad = tc::sdesc(st + kA[pr] * TILE_BYTES + ks * 256, 128, SBO);
-          const uint64_t bd = tc::sdesc(st + (3 + kB[pr]) * TILE_BYTES + ks * 256, 128, SBO);
+          const uint64_t ad = tc::sdesc(st + kA[pr] * A_BYTES + ks * 256, 128, SBO);
+          const uint64_t bd = tc::sdesc(st + 3 * A_BYTES + kB[pr] * B_BYTES + ks * 256, 128, SBO);
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tm),
@@ -132,20 +137,20 @@ __global__ void __launch_bounds__(gtc::THREADS, 1) k_gemm_tc(const __grid_consta
     atomicCAS(g.status, 0, (int)FS_ERR_TIMEOUT);
   tc::fence_after();
 
-  // epilogue: warp w reads lanes 32 (w mod 4) .. and columns 64 (w / 4) ..
+  // epilogue: warp w reads lanes 32 (w mod 4) .. and columns 128 (w / 4) ..
   const int q = warp & 3, h = warp >> 2;
   const int m = m0 + 32 * q + lane;
   const uint32_t lanes = (uint32_t)(32 * q) << 16;
 #pragma unroll 1
-  for (int c0 = 0; c0 < 64; c0 += 16) {
+  for (int c0 = 0; c0 < BN / 2; c0 += 16) {
     uint32_t v[2][8];
-    tc::tmem_ld8(tm + lanes + (uint32_t)(64 * h + c0), v[0]);
-    tc::tmem_ld8(tm + lanes + (uint32_t)(64 * h + c0 + 8), v[1]);
+    tc::tmem_ld8(tm + lanes + (uint32_t)(BN / 2 * h + c0), v[0]);
+    tc::tmem_ld8(tm + lanes + (uint32_t)(BN / 2 * h + c0 + 8), v[1]);
     tc::wait_ld();
     if (m >= g.M || nk == 0) continue;
 #pragma unroll
     for (int j = 0; j < 16; j += 2) {
-      const int n = n0 + 64 * h + c0 + j;
+      const int n = n0 + BN / 2 * h + c0 + j;
       const float x0 = __uint_as_float(v[j >> 3][j & 7]);
       const float x1 = __uint_as_float(v[(j + 1) >> 3][(j + 1) & 7]);
       switch (g.mode) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <complex>
 #include <map>
 #include <tuple>
@@ -191,6 +192,15 @@ struct Ctx {
   int device = 0;
   // autotuned orbital-rotation method per (norb, n_alpha, n_beta, dtype)
   std::map<std::tuple<int, int, int, int>, int> rot_choice;
+  // autotuned slab width (log2 of vectors per CTA) of the batched sweeps per
+  // (norb, electrons of the rotated and the other spin, dtype, states,
+  // reverse, cross term, shared-memory budget in KB), and the timings behind
+  // each choice (ms per launch for lgKV = 0, 1, ...); tuned on first use on
+  // a private stream
+  std::map<std::array<int, 8>, int> sweep_tune;
+  std::map<std::array<int, 8>, std::vector<float>> sweep_tune_ms;
+  cudaStream_t tune_stream = nullptr;
+  int batch_tuning = 1;
   bool prof_on = false;
   std::vector<ProfRec> prof;
   cudaDeviceProp prop{};

@@ -136,78 +136,138 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// The minor matrix M[J][I] = det(U[J, I]) in the real form of a complex
-// right operand, as three BF16 planes (row stride ld): row 2J + x, column
-// 2I + y holds [[Re, -Im], [Im, Re]][x][y] of M[J][I], split from FP64 into
-// the nearest BF16 of each remainder.  One thread per (J, I).
-__global__ void k_minor_planes(const uint32_t* masks, int64_t d, int norb, int n,
-                               const __grid_constant__ CMat U, __nv_bfloat16* p0,
-                               __nv_bfloat16* p1, __nv_bfloat16* p2, int64_t ld) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= d * d) return;
-  const int64_t J = t / d, I = t - J * d;
-  double2 a[kMinorMaxN * kMinorMaxN];
-  const uint32_t mj = masks[J], mi = masks[I];
-  int r = 0;
-  for (int p = 0; p < norb; ++p) {
-    if (!((mj >> p) & 1u)) continue;
-    int c = 0;
-    for (int q = 0; q < norb; ++q) {
-      if (!((mi >> q) & 1u)) continue;
-      a[r * n + c] = make_double2(U.v[2 * (p * norb + q)], U.v[2 * (p * norb + q) + 1]);
-      ++c;
-    }
-    ++r;
+// det(U[rows of mj, columns of mi]) for NE electrons, FP64 Gaussian
+// elimination with partial pivoting (on the squared modulus) in registers.
+template <int NE>
+__device__ __forceinline__ double2 minor_det(uint32_t mj, uint32_t mi, int norb, const double* Uv) {
+  if constexpr (NE == 0) {
+    return make_double2(1, 0);
+  } else {
+  int rows[NE], cols[NE];
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    rows[k] = __ffs(mj) - 1;
+    mj &= mj - 1;
+    cols[k] = __ffs(mi) - 1;
+    mi &= mi - 1;
   }
+  double2 a[NE][NE];
+#pragma unroll
+  for (int r = 0; r < NE; ++r)
+#pragma unroll
+    for (int c = 0; c < NE; ++c) {
+      const int o = 2 * (rows[r] * norb + cols[c]);
+      a[r][c] = make_double2(Uv[o], Uv[o + 1]);
+    }
   double dr = 1, di = 0;
-  for (int k = 0; k < n; ++k) {
+  bool singular = false;
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
     int piv = k;
-    double best = hypot(a[k * n + k].x, a[k * n + k].y);
-    for (int i = k + 1; i < n; ++i) {
-      const double h = hypot(a[i * n + k].x, a[i * n + k].y);
+    double best = a[k][k].x * a[k][k].x + a[k][k].y * a[k][k].y;
+#pragma unroll
+    for (int i = k + 1; i < NE; ++i) {
+      const double h = a[i][k].x * a[i][k].x + a[i][k].y * a[i][k].y;
       if (h > best) {
         best = h;
         piv = i;
       }
     }
-    if (best == 0) {
-      dr = di = 0;
-      break;
+    singular = singular || best == 0;
+    // row swap k <-> piv by selects, so that every index stays compile-time
+#pragma unroll
+    for (int i = k + 1; i < NE; ++i) {
+      const bool sw = i == piv;
+#pragma unroll
+      for (int c = k; c < NE; ++c) {
+        const double2 tk = a[k][c], ti = a[i][c];
+        a[k][c] = sw ? ti : tk;
+        a[i][c] = sw ? tk : ti;
+      }
     }
     if (piv != k) {
-      for (int c = 0; c < n; ++c) {
-        const double2 tmp = a[k * n + c];
-        a[k * n + c] = a[piv * n + c];
-        a[piv * n + c] = tmp;
-      }
       dr = -dr;
       di = -di;
     }
-    const double2 pk = a[k * n + k];
+    const double2 pk = a[k][k];
     const double nr = dr * pk.x - di * pk.y;
     di = dr * pk.y + di * pk.x;
     dr = nr;
-    const double inv = 1.0 / (pk.x * pk.x + pk.y * pk.y);
-    for (int i = k + 1; i < n; ++i) {
-      const double2 x = a[i * n + k];
+    const double inv = best > 0 ? 1.0 / best : 0.0;
+#pragma unroll
+    for (int i = k + 1; i < NE; ++i) {
+      const double2 x = a[i][k];
       const double fr = (x.x * pk.x + x.y * pk.y) * inv, fi = (x.y * pk.x - x.x * pk.y) * inv;
-      for (int c = k + 1; c < n; ++c) {
-        const double2 y = a[k * n + c];
-        a[i * n + c].x -= fr * y.x - fi * y.y;
-        a[i * n + c].y -= fr * y.y + fi * y.x;
+#pragma unroll
+      for (int c = k + 1; c < NE; ++c) {
+        const double2 y = a[k][c];
+        a[i][c].x -= fr * y.x - fi * y.y;
+        a[i][c].y -= fr * y.y + fi * y.x;
       }
     }
   }
-  const double ent[4] = {dr, -di, di, dr};
+  return singular ? make_double2(0, 0) : make_double2(dr, di);
+  }
+}
+
+// The minor matrix M[J][I] = det(U[J, I]) in the real form of a complex
+// right operand, as three BF16 planes (row stride ld): row 2J + x, column
+// 2I + y holds [[Re, -Im], [Im, Re]][x][y] of M[J][I], split from FP64 into
+// the nearest BF16 of each remainder.  One thread per (J, I).
+template <int NE>
+__global__ void k_minor_planes(const uint32_t* masks, int64_t d, int norb,
+                               const __grid_constant__ CMat U, __nv_bfloat16* p0,
+                               __nv_bfloat16* p1, __nv_bfloat16* p2, int64_t ld) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= d * d) return;
+  const int64_t J = t / d, I = t - J * d;
+  const double2 v = minor_det<NE>(masks[J], masks[I], norb, U.v);
+  const double ent[4] = {v.x, -v.y, v.y, v.x};
   __nv_bfloat16* planes[3] = {p0, p1, p2};
+#pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int64_t off = (2 * J + (e >> 1)) * ld + 2 * I + (e & 1);
     double rem = ent[e];
+#pragma unroll
     for (int pc = 0; pc < 3; ++pc) {
       const __nv_bfloat16 b = __float2bfloat16_rn((float)rem);
       planes[pc][off] = b;
       rem -= (double)__bfloat162float(b);
     }
+  }
+}
+
+template <int NE>
+static void minor_planes_n(const Space* sp, const CMat& U, uint16_t* B, size_t plane, int64_t ld,
+                           cudaStream_t st) {
+  const int64_t d = sp->dim;
+  k_minor_planes<NE><<<(unsigned)((d * d + 127) / 128), 128, 0, st>>>(
+      sp->masks, d, sp->norb, U, (__nv_bfloat16*)B, (__nv_bfloat16*)(B + plane),
+      (__nv_bfloat16*)(B + 2 * plane), ld);
+  FS_CUDA(cudaGetLastError());
+}
+
+static void minor_planes(const Space* sp, const CMat& U, uint16_t* B, size_t plane, int64_t ld,
+                         cudaStream_t st) {
+  switch (sp->nocc) {
+    case 0: minor_planes_n<0>(sp, U, B, plane, ld, st); break;
+    case 1: minor_planes_n<1>(sp, U, B, plane, ld, st); break;
+    case 2: minor_planes_n<2>(sp, U, B, plane, ld, st); break;
+    case 3: minor_planes_n<3>(sp, U, B, plane, ld, st); break;
+    case 4: minor_planes_n<4>(sp, U, B, plane, ld, st); break;
+    case 5: minor_planes_n<5>(sp, U, B, plane, ld, st); break;
+    case 6: minor_planes_n<6>(sp, U, B, plane, ld, st); break;
+    case 7: minor_planes_n<7>(sp, U, B, plane, ld, st); break;
+    case 8: minor_planes_n<8>(sp, U, B, plane, ld, st); break;
+    case 9: minor_planes_n<9>(sp, U, B, plane, ld, st); break;
+    case 10: minor_planes_n<10>(sp, U, B, plane, ld, st); break;
+    case 11: minor_planes_n<11>(sp, U, B, plane, ld, st); break;
+    case 12: minor_planes_n<12>(sp, U, B, plane, ld, st); break;
+    case 13: minor_planes_n<13>(sp, U, B, plane, ld, st); break;
+    case 14: minor_planes_n<14>(sp, U, B, plane, ld, st); break;
+    case 15: minor_planes_n<15>(sp, U, B, plane, ld, st); break;
+    case 16: minor_planes_n<16>(sp, U, B, plane, ld, st); break;
+    default: FS_REQUIRE(false, FS_ERR_UNSUPPORTED, "at most 16 electrons per spin");
   }
 }
 
@@ -225,18 +285,10 @@ static void minor_rotation_tc(Ctx* ctx, const Space* sa, const Space* sb, void* 
   uint16_t* Ap = (uint16_t*)scratch(ctx, "minor_tc_psi", 3 * ppsi * 2);
   uint16_t* Tp = (uint16_t*)scratch(ctx, "minor_tc_tmp", 3 * ptmp * 2);
   {
+    // (padding columns past K are never read: the GEMM loads stop at K)
     ProfScope ps("minor_matrices", st, 2);
-    FS_CUDA(cudaMemsetAsync(Ba, 0, 3 * pa * 2, st));
-    FS_CUDA(cudaMemsetAsync(Bb, 0, 3 * pb * 2, st));
-    FS_CUDA(cudaMemsetAsync(Tp, 0, 3 * ptmp * 2, st));
-    k_minor_planes<<<(unsigned)((da * da + 127) / 128), 128, 0, st>>>(
-        sa->masks, da, sa->norb, sa->nocc, Ua, (__nv_bfloat16*)Ba, (__nv_bfloat16*)(Ba + pa),
-        (__nv_bfloat16*)(Ba + 2 * pa), lka);
-    FS_CUDA(cudaGetLastError());
-    k_minor_planes<<<(unsigned)((db * db + 127) / 128), 128, 0, st>>>(
-        sb->masks, db, sb->norb, sb->nocc, Ub, (__nv_bfloat16*)Bb, (__nv_bfloat16*)(Bb + pb),
-        (__nv_bfloat16*)(Bb + 2 * pb), lkb);
-    FS_CUDA(cudaGetLastError());
+    minor_planes(sa, Ua, Ba, pa, lka, st);
+    minor_planes(sb, Ub, Bb, pb, lkb, st);
   }
   ProfScope ps("minor_gemm_tc", st, 3);
   void* psi_planes[3] = {Ap, Ap + ppsi, Ap + 2 * ppsi};

@@ -294,13 +294,16 @@ void launch_phase_tc(Ctx* ctx, const Space* sa, const Space* sb, void* vec, cons
                                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   FS_REQUIRE(r == CUDA_SUCCESS, FS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the state");
-  ProfScope ps("phase_tc_f32", st, 3);
+  {
+  ProfScope ps("dc_tables", st, 2);
   k_dc_occ<<<(unsigned)((nti * TI + 127) / 128), 128, 0, st>>>(
       occ, eaa, sa->masks, (const float2*)ph.ea_a, da, nti, nk);
   FS_CUDA(cudaGetLastError());
   k_dc_ypieces<<<(unsigned)((ntj * TJ + 127) / 128), 128, 0, st>>>(
       ypc, eab, sb->masks, (const float2*)ph.ea_b, db, ntj, sa->norb, nk, ph.X);
   FS_CUDA(cudaGetLastError());
+  }
+  ProfScope ps("phase_tc_f32", st);
   const int sstride = (stage_bytes(nk) + 1023) / 1024 * 1024;
   const size_t smem = (size_t)STAGES * sstride + 1024;
   const int64_t ntiles = nti * ntj;

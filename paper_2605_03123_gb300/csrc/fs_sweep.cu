@@ -1643,6 +1643,73 @@ int batch_window(int dtype, int nst) {
 // One circuit's sweep as a job of a batched launch: one CTA per slab (no
 // cluster), window program for the batch window width, slab sized to
 // `budget` bytes of shared memory.
+// Autotuner of the batched sweeps' slab width: one circuit's sweep as a
+// one-job launch of the batched kernel, on scratch states (and scratch W
+// and T for the reverse sweeps), for every slab width 2^0 .. 2^lgmax that
+// fits the stage's budget; CUDA events on a private stream, the fastest
+// mean of two launches after one warm-up wins and is cached per sector and
+// sweep kind.  Runs before any capture.
+template <typename SmemFor>
+static int tune_batch_slab(Ctx* ctx, const SweepGeom& g0, const std::vector<unsigned char>& prog,
+                           int nst, int dtype, bool rev, int lgmax, SmemFor&& smem_for,
+                           const std::array<int, 8>& key) {
+  if (!ctx->tune_stream)
+    FS_CUDA(cudaStreamCreateWithFlags(&ctx->tune_stream, cudaStreamNonBlocking));
+  cudaStream_t ts = ctx->tune_stream;
+  const size_t csz = dtype == FS_C64 ? 8 : 16;
+  const size_t nstate = (size_t)g0.d * g0.nvec;
+  char* st = (char*)scratch(ctx, "tune_states", nstate * csz * nst);
+  FS_CUDA(cudaMemsetAsync(st, 0, nstate * csz * nst, ts));
+  // device copies of the program, a zero cross matrix and the job
+  char* dev = (char*)scratch(ctx, "tune_job", prog.size() + sizeof(Mat) + sizeof(SweepJob) + 1024);
+  char* dprog = dev;
+  Mat* dX = (Mat*)(dev + (prog.size() + 255) / 256 * 256);
+  SweepJob* djob = (SweepJob*)((char*)dX + (sizeof(Mat) + 255) / 256 * 256);
+  int* dcounter = (int*)scratch(ctx, "tune_counter", sizeof(int));
+  FS_CUDA(cudaMemcpyAsync(dprog, prog.data(), prog.size(), cudaMemcpyHostToDevice, ts));
+  FS_CUDA(cudaMemsetAsync(dX, 0, sizeof(Mat), ts));
+  SweepGeom g = g0;
+  g.st[0] = st;
+  g.st[1] = nst == 2 ? st + nstate * csz : nullptr;
+  if (rev) {
+    g.T = (double*)scratch(ctx, "tune_T", (size_t)2 * kMaxOrb * kMaxOrb * sizeof(double));
+    g.W = g0.W ? scratch(ctx, "tune_W", nstate * (csz / 2)) : nullptr;
+  }
+  cudaEvent_t e0, e1;
+  FS_CUDA(cudaEventCreate(&e0));
+  FS_CUDA(cudaEventCreate(&e1));
+  std::vector<float> ms(lgmax + 1, 0.f);
+  int best = 0;
+  for (int lg = 0; lg <= lgmax; ++lg) {
+    g.lgKV = lg;
+    SweepJob j{};
+    j.g = g;
+    j.prog = dprog;
+    j.X = dX;
+    j.item0 = 0;
+    const int nslabs = (g.nvec + (1 << lg) - 1) >> lg;
+    const size_t smem = smem_for(1 << lg);
+    FS_CUDA(cudaMemcpyAsync(djob, &j, sizeof(j), cudaMemcpyHostToDevice, ts));
+    launch_sweep_batch(ctx, dtype, nst, nullptr, 0, 0, nullptr, smem, ts);  // attribute
+    float tot = 0;
+    for (int r = 0; r < 3; ++r) {
+      FS_CUDA(cudaMemsetAsync(dcounter, 0, sizeof(int), ts));
+      if (r == 1) FS_CUDA(cudaEventRecord(e0, ts));
+      launch_sweep_batch(ctx, dtype, nst, djob, 1, nslabs, dcounter, smem, ts);
+    }
+    FS_CUDA(cudaEventRecord(e1, ts));
+    FS_CUDA(cudaEventSynchronize(e1));
+    FS_CUDA(cudaEventElapsedTime(&tot, e0, e1));
+    ms[lg] = tot / 2;
+    if (ms[lg] < ms[best]) best = lg;
+  }
+  FS_CUDA(cudaEventDestroy(e0));
+  FS_CUDA(cudaEventDestroy(e1));
+  ctx->sweep_tune[key] = best;
+  ctx->sweep_tune_ms[key] = ms;
+  return best;
+}
+
 void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* st1, int nst,
                       int dtype, const RotProgram& rp, const PhaseDev& ph, const RevArgs* rev,
                       size_t budget, BatchSweepPlan& out) {
@@ -1687,24 +1754,38 @@ void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* 
     return (size_t)KV * ((size_t)g.d * csz * nst + tab_per_kv + fixed) + tsum;
   };
   FS_REQUIRE(smem_for(1) <= budget, FS_ERR_UNSUPPORTED, "batched sweep slab does not fit");
-  int want = std::max(1, g.nvec / 8);
-  int lg = 0;
-  while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(2 << lg) <= budget) ++lg;
-  g.lgKV = lg;
   g.chunk = g.d;
   g.cb[0] = 0;
   g.cb[1] = g.d;
-  out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
-  out.smem = smem_for(1 << lg);
+  out.prog.resize(wprog_bytes(dtype));
   if (dtype == FS_C64) {
-    out.prog.resize(wprog_bytes(dtype));
     auto w = make_wprog<float>(rp, sthis->norb, W);
     memcpy(out.prog.data(), &w, sizeof(w));
   } else {
-    out.prog.resize(wprog_bytes(dtype));
     auto w = make_wprog<double>(rp, sthis->norb, W);
     memcpy(out.prog.data(), &w, sizeof(w));
   }
+  // slab width: the widest that fits the budget (at most 64 vectors), or the
+  // autotuned width for this sector and sweep kind
+  int lgmax = 0;
+  while ((2 << lgmax) <= std::min(g.nvec, kMaxKV) && smem_for(2 << lgmax) <= budget) ++lgmax;
+  const std::array<int, 8> key = {sthis->norb, sthis->nocc, sother->nocc, dtype, nst,
+                                  rev != nullptr, ph.has_x, (int)(budget >> 10)};
+  int lg = -1;
+  auto it = ctx->sweep_tune.find(key);
+  if (it != ctx->sweep_tune.end()) {
+    lg = std::min(it->second, lgmax);
+  } else if (ctx->batch_tuning && lgmax > 0) {
+    lg = tune_batch_slab(ctx, g, out.prog, nst, dtype, rev != nullptr, lgmax, smem_for, key);
+  }
+  if (lg < 0) {  // untuned: about eight slabs per circuit
+    const int want = std::max(1, g.nvec / 8);
+    lg = 0;
+    while ((2 << lg) <= std::min(want, kMaxKV) && lg < lgmax) ++lg;
+  }
+  g.lgKV = lg;
+  out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
+  out.smem = smem_for(1 << lg);
 }
 
 template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT>

@@ -72,6 +72,8 @@ SIGNATURES = {
     "fs_sample_state": [_P, _P, _I, _I, _I, _I, _P, _I64, _P, _P],
     "fs_sample_slater": [_P, _P, _I, _P, _I, _P, _I64, _P, _P],
     "fs_set_sweep_engine": [_P, _I],
+    "fs_set_batch_tuning": [_P, _I],
+    "fs_tuning_report": [_P, _P, _I64],
     "fs_measure_fp32_fma": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "fs_lucj_batch": [_P, _I, ctypes.POINTER(LUCJ), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                       _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
@@ -125,6 +127,16 @@ class Context:
 
     def set_sweep_engine(self, engine):
         _check("fs_set_sweep_engine", load_library().fs_set_sweep_engine(self.handle, int(engine)))
+
+    def set_batch_tuning(self, on):
+        _check("fs_set_batch_tuning", load_library().fs_set_batch_tuning(self.handle, int(bool(on))))
+
+    def tuning_report(self):
+        """The batched-sweep autotuner's choices, one dict per sector and sweep kind."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check("fs_tuning_report", load_library().fs_tuning_report(self.handle, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def sync_status(self, stream=None):
         """The device status word (FS_OK, or FS_ERR_TIMEOUT / FS_ERR_BOUNDS

@@ -102,3 +102,33 @@ def test_batch_rejects_mixed_reps(lib):
     vecs = [dev(_start(c), "c64") for c in cir]
     with pytest.raises(lib.FsError):
         lib.lucj_batch_(vecs, None, cir, do_vjp=False)
+
+
+def test_batch_autotuner_choices_and_results(lib):
+    """The slab-width autotuner picks, per sector and sweep kind, one of the
+    timed widths (the fastest), and a tuned batch gives the same states and
+    gradients as an untuned one."""
+    ctx = lib.context(0)
+    cir = _circuits(17000)
+    res = {}
+    for on in (0, 1):
+        ctx.set_batch_tuning(on)
+        vecs = [dev(_start(c), "c64") for c in cir]
+        cots = [dev(c["c"], "c64") for c in cir]
+        grads = lib.lucj_batch_(vecs, cots, cir, do_vjp=True, ctx=ctx)
+        res[on] = ([host(x) for x in vecs], [host(y) for y in cots], grads)
+        if on:
+            rep = ctx.tuning_report()
+            assert rep, "the autotuner recorded no choice"
+            for r in rep:
+                ms = r["ms"]
+                assert len(ms) >= 2 and all(t > 0 for t in ms)
+                assert r["vectors_per_cta"] == 1 << int(np.argmin(ms))
+    ctx.set_batch_tuning(1)
+    for a, b in zip(res[0][0], res[1][0]):
+        assert np.max(np.abs(a - b)) < 2e-5
+    for a, b in zip(res[0][1], res[1][1]):
+        assert np.max(np.abs(a - b)) < 2e-5
+    for ga, gb in zip(res[0][2], res[1][2]):
+        for a, b in zip(ga, gb):
+            assert _rel(a, b) < 1e-4
