@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libfsgpu.so"
-SOURCES = ["fs_api.cu", "fs_tables.cu", "fs_sweep.cu", "fs_reduce.cu", "fs_minor.cu",
+SOURCES = ["fs_api.cu", "fs_tables.cu", "fs_sweep.cu", "fs_sweep_f32fwd.cu", "fs_sweep_f32rev.cu",
+           "fs_sweep_f32batch.cu", "fs_reduce.cu", "fs_minor.cu",
            "fs_phase_tc.cu", "fs_batch.cu", "fs_operator.cu", "fs_noalloc.cu", "fs_sample.cu", "fs_peak.cu", "fs_gemm_tc.cu",
            "fs_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -9,16 +9,22 @@
 // six products A_i B_j with i + j <= 4 over the pieces are accumulated in
 // TMEM (FP32); the dropped products are below 2^-24 of the result.
 //
-// A CTA computes a 128 x 256 tile of C: K is walked in chunks of 32, each
-// chunk's six piece-tiles (A1..A3: 8 KB each, B1..B3: 16 KB each) copied by
-// cp.async into a three-stage shared-memory ring in the K-major no-swizzle
-// core-matrix layout (8 rows x 16 bytes per core matrix, LBO = 128 B along
-// K, SBO = 512 B between 8-row groups); one thread issues the 12 MMAs of a
-// chunk (128 x 256 x 16 each) and commits them to the stage's mbarrier,
-// which frees the stage for the chunk two ahead.  The epilogue reads the
-// tile from TMEM (warp w: lanes 32 (w mod 4), columns 128 (w / 4) ..) and
-// writes it in one of the output forms below.  Waits are bounded (status
-// word FS_ERR_TIMEOUT on give-up); the TMEM is always freed.
+// The kernel is persistent (one CTA per SM, tiles of 128 x 256 of C dealt
+// round-robin, consecutive CTAs on the same column panel so the B panel is
+// shared in L2) and warp-specialized:
+//   * warp 0 (one thread) streams K in chunks of 32 through a three-stage
+//     shared-memory ring: per chunk six 2-D TMA loads (A1..A3: 128 x 32,
+//     B1..B3: 256 x 32 BF16, 64-byte swizzle, out-of-range rows and k read as
+//     zeros) completing on the stage's "full" mbarrier;
+//   * warp 1 (one thread) issues the chunk's twelve MMAs (six products x two
+//     K steps of 16, 128 x 256 each) into one of two TMEM accumulators
+//     (2 x 256 columns) and commits them to the stage's "empty" mbarrier, and
+//     after a tile's last chunk to the accumulator's "full" mbarrier;
+//   * warps 2..5 (TMEM lanes 32 (w mod 4) ..) drain an accumulator with
+//     tcgen05.ld, write it in one of the output forms below, and release it,
+//     so the epilogue of one tile overlaps the products of the next.
+// Every wait is bounded (status word FS_ERR_TIMEOUT on give-up); the TMEM is
+// always freed.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -30,161 +36,172 @@
 namespace fs {
 namespace gtc {
 
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3, THREADS = 256;
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3;
+constexpr int THREADS = 192;                 // TMA warp, MMA warp, 4 epilogue warps
 constexpr int A_BYTES = BM * BK * 2;         // one BF16 piece of A: 8 KB
 constexpr int B_BYTES = BN * BK * 2;         // one BF16 piece of B: 16 KB
 constexpr int STAGE_BYTES = 3 * A_BYTES + 3 * B_BYTES;
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-constexpr uint32_t SBO = (BK / 8) * 128;
+// 64-byte swizzle, K-major: rows of BK = 32 BF16 (64 bytes), 8-row atoms of
+// 512 bytes; the K step of 16 inside a row advances the start by 32 bytes
+constexpr uint32_t SBO = 8 * BK * 2;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
-constexpr int A_CHUNKS = BM * BK / 8, B_CHUNKS = BN * BK / 8;  // 16-byte copies per piece
+
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)(SBO >> 4) << 32) |
+         (1ull << 46) | (4ull << 61);
+}
 
 }  // namespace gtc
 
-__global__ void __launch_bounds__(gtc::THREADS, 1) k_gemm_tc(const __grid_constant__ GemmTc g) {
+struct GemmMaps {
+  CUtensorMap a[3], b[3];
+};
+
+__global__ void __launch_bounds__(gtc::THREADS, 1)
+    k_gemm_tc(const __grid_constant__ GemmMaps maps, const __grid_constant__ GemmTc g,
+              int tiles_m, int tiles) {
   using namespace gtc;
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t s_mbar[STAGES];
+  __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_accf[2], s_acce[2];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const uint32_t sraw = tc::smem_u32(smraw);
-  const uint32_t sbase = (sraw + 1023u) & ~1023u;
+  const uint32_t sbase = (tc::smem_u32(smraw) + 1023u) & ~1023u;
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) tc::mbar_init(tc::smem_u32(&s_mbar[s]), 1);
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(tc::smem_u32(&s_full[s]), 1);
+      tc::mbar_init(tc::smem_u32(&s_empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(tc::smem_u32(&s_accf[a]), 1);
+      tc::mbar_init(tc::smem_u32(&s_acce[a]), 4);
+    }
     tc::mbar_fence_init();
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), BN);
+  if (warp == 1) tc::tmem_alloc(tc::smem_u32(&s_tmem), 2 * BN);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tm = s_tmem;
   const int nk = (g.K + BK - 1) / BK;
+  bool ok = true;
 
-  // chunk kc of all six pieces into stage s (rows past M / N and k past K
-  // read as zeros)
-  auto load = [&](int kc, int s) {
-    const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
-    const int k0 = kc * BK;
-    for (int c = tid; c < 3 * (A_CHUNKS + B_CHUNKS); c += THREADS) {
-      const bool isA = c < 3 * A_CHUNKS;
-      const int cb = isA ? c : c - 3 * A_CHUNKS;
-      const int piece = isA ? cb / A_CHUNKS : cb / B_CHUNKS;
-      const int cc = isA ? cb - piece * A_CHUNKS : cb - piece * B_CHUNKS;
-      const int r = ((cc >> 5) << 3) | (cc & 7), kq = (cc >> 3) & 3;
-      const int row = (isA ? m0 : n0) + r;
-      const uint16_t* src = isA ? g.A[piece] : g.B[piece];
-      const int64_t ld = isA ? g.lda : g.ldb;
-      const int kk = k0 + kq * 8;
-      int bytes = 0;
-      if (row < (isA ? g.M : g.N) && kk < g.K) bytes = min(8, g.K - kk) * 2;
-      const uint16_t* gp = bytes ? src + (int64_t)row * ld + kk : src;
-      const uint32_t base = isA ? (uint32_t)(piece * A_BYTES)
-                                : (uint32_t)(3 * A_BYTES + piece * B_BYTES);
-      const uint32_t dst = st + base + (uint32_t)((r >> 3) * SBO) +
-                           (uint32_t)(kq * 128 + (r & 7) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gp),
-                   "r"(bytes)
-                   : "memory");
-    }
-  };
-  for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < nk) load(s, s);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  for (int kc = 0; kc < nk; ++kc) {
-    const int s = kc % STAGES;
-    asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
-      constexpr int kA[6] = {2, 1, 0, 1, 0, 0};
-      constexpr int kB[6] = {0, 1, 2, 0, 1, 0};
+  if (warp == 0) {
+    if (lane == 0) {
+      int i = 0;  // chunk counter over all tiles of this CTA
+      for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+        for (int kc = 0; kc < nk; ++kc, ++i) {
+          const int s = i % STAGES, u = i / STAGES;
+          if (u >= 1 && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), (uint32_t)(u - 1) & 1u))
+            ok = false;
+          const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
+          const uint32_t fb = tc::smem_u32(&s_full[s]);
+          tc::mbar_expect_tx(fb, STAGE_BYTES);
 #pragma unroll
-      for (int pr = 0; pr < 6; ++pr)
+          for (int p = 0; p < 3; ++p) tc::tma_load_2d(st + p * A_BYTES, &maps.a[p], kc * BK, m0, fb);
 #pragma unroll
-        for (int ks = 0; ks < BK / 16; ++ks) {
-          const uint64_t ad = tc::sdesc(st + kA[pr] * A_BYTES + ks * 256, 128, SBO);
-          const uint64_t bd = tc::sdesc(st + 3 * A_BYTES + kB[pr] * B_BYTES + ks * 256, 128, SBO);
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tm),
-              "l"(ad), "l"(bd), "r"(IDESC), "r"((kc > 0 || pr > 0 || ks > 0) ? 1u : 0u)
-              : "memory");
+          for (int p = 0; p < 3; ++p)
+            tc::tma_load_2d(st + 3 * A_BYTES + p * B_BYTES, &maps.b[p], kc * BK, n0, fb);
         }
-      tc::mma_commit(tc::smem_u32(&s_mbar[s]));
-    }
-    // chunk kc + STAGES - 1 refills the stage of chunk kc - 1 once its
-    // products are done
-    const int kn = kc + STAGES - 1;
-    if (kn < nk) {
-      const int sn = kn % STAGES;
-      if (kc >= 1 &&
-          !tc::mbar_wait(tc::smem_u32(&s_mbar[sn]), (uint32_t)((kc - 1) / STAGES) & 1u) &&
-          g.status)
-        atomicCAS(g.status, 0, (int)FS_ERR_TIMEOUT);
-      load(kn, sn);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (nk > 0 && !tc::mbar_wait(tc::smem_u32(&s_mbar[(nk - 1) % STAGES]),
-                               (uint32_t)((nk - 1) / STAGES) & 1u) &&
-      g.status)
-    atomicCAS(g.status, 0, (int)FS_ERR_TIMEOUT);
-  tc::fence_after();
-
-  // epilogue: warp w reads lanes 32 (w mod 4) .. and columns 128 (w / 4) ..
-  const int q = warp & 3, h = warp >> 2;
-  const int m = m0 + 32 * q + lane;
-  const uint32_t lanes = (uint32_t)(32 * q) << 16;
-#pragma unroll 1
-  for (int c0 = 0; c0 < BN / 2; c0 += 16) {
-    uint32_t v[2][8];
-    tc::tmem_ld8(tm + lanes + (uint32_t)(BN / 2 * h + c0), v[0]);
-    tc::tmem_ld8(tm + lanes + (uint32_t)(BN / 2 * h + c0 + 8), v[1]);
-    tc::wait_ld();
-    if (m >= g.M || nk == 0) continue;
-#pragma unroll
-    for (int j = 0; j < 16; j += 2) {
-      const int n = n0 + BN / 2 * h + c0 + j;
-      const float x0 = __uint_as_float(v[j >> 3][j & 7]);
-      const float x1 = __uint_as_float(v[(j + 1) >> 3][(j + 1) & 7]);
-      switch (g.mode) {
-        case GEMM_REAL:
-          if (n < g.N) reinterpret_cast<float*>(g.out)[(int64_t)m * g.ldo + n] = x0;
-          if (n + 1 < g.N) reinterpret_cast<float*>(g.out)[(int64_t)m * g.ldo + n + 1] = x1;
-          break;
-        case GEMM_REAL_T:
-          if (n < g.N) reinterpret_cast<float*>(g.out)[(int64_t)n * g.ldo + m] = x0;
-          if (n + 1 < g.N) reinterpret_cast<float*>(g.out)[(int64_t)(n + 1) * g.ldo + m] = x1;
-          break;
-        case GEMM_CPLX_T:
-          if (n + 1 < g.N)
-            reinterpret_cast<float2*>(g.out)[(int64_t)(n >> 1) * g.ldo + m] = make_float2(x0, x1);
-          break;
-        case GEMM_CPLX_T_PLANES:
-          if (n + 1 < g.N) {
-            uint32_t p1, p2, p3;
-            tc::split_bf16x3(x0, x1, p1, p2, p3);
-            const int64_t w = ((int64_t)(n >> 1) * g.ldp + 2 * m) >> 1;
-            reinterpret_cast<uint32_t*>(g.outp[0])[w] = p1;
-            reinterpret_cast<uint32_t*>(g.outp[1])[w] = p2;
-            reinterpret_cast<uint32_t*>(g.outp[2])[w] = p3;
-          }
-          break;
-        default: break;
       }
     }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0, j = 0;
+      for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+        const int a = j & 1, v = j >> 1;
+        if (v >= 1 && !tc::mbar_wait(tc::smem_u32(&s_acce[a]), (uint32_t)(v - 1) & 1u)) ok = false;
+        tc::fence_after();
+        const uint32_t d = tm + (uint32_t)(a * BN);
+        for (int kc = 0; kc < nk; ++kc, ++i) {
+          const int s = i % STAGES, u = i / STAGES;
+          if (!tc::mbar_wait(tc::smem_u32(&s_full[s]), (uint32_t)u & 1u)) ok = false;
+          tc::fence_after();
+          const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
+          constexpr int kA[6] = {2, 1, 0, 1, 0, 0};
+          constexpr int kB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+          for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+              const uint64_t ad = sdesc_sw64(st + kA[pr] * A_BYTES + ks * 32);
+              const uint64_t bd = sdesc_sw64(st + 3 * A_BYTES + kB[pr] * B_BYTES + ks * 32);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(ad), "l"(bd), "r"(IDESC), "r"((kc > 0 || pr > 0 || ks > 0) ? 1u : 0u)
+                  : "memory");
+            }
+          tc::mma_commit(tc::smem_u32(&s_empty[s]));
+        }
+        tc::mma_commit(tc::smem_u32(&s_accf[a]));
+      }
+    }
+  } else {
+    // epilogue: this warp's TMEM lane quadrant, all 256 columns of a tile
+    const int q = warp & 3;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    int j = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+      const int a = j & 1, v = j >> 1;
+      if (!tc::mbar_wait(tc::smem_u32(&s_accf[a]), (uint32_t)v & 1u)) ok = false;
+      tc::fence_after();
+      const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+      const int m = m0 + 32 * q + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t vv[2][8];
+        tc::tmem_ld8(tm + lanes + (uint32_t)(a * BN + c0), vv[0]);
+        tc::tmem_ld8(tm + lanes + (uint32_t)(a * BN + c0 + 8), vv[1]);
+        tc::wait_ld();
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int jj = 0; jj < 16; jj += 2) {
+          const int n = n0 + c0 + jj;
+          const float x0 = __uint_as_float(vv[jj >> 3][jj & 7]);
+          const float x1 = __uint_as_float(vv[(jj + 1) >> 3][(jj + 1) & 7]);
+          switch (g.mode) {
+            case GEMM_REAL:
+              if (n < g.N) reinterpret_cast<float*>(g.out)[(int64_t)m * g.ldo + n] = x0;
+              if (n + 1 < g.N) reinterpret_cast<float*>(g.out)[(int64_t)m * g.ldo + n + 1] = x1;
+              break;
+            case GEMM_REAL_T:
+              if (n < g.N) reinterpret_cast<float*>(g.out)[(int64_t)n * g.ldo + m] = x0;
+              if (n + 1 < g.N)
+                reinterpret_cast<float*>(g.out)[(int64_t)(n + 1) * g.ldo + m] = x1;
+              break;
+            case GEMM_CPLX_T:
+              if (n + 1 < g.N)
+                reinterpret_cast<float2*>(g.out)[(int64_t)(n >> 1) * g.ldo + m] =
+                    make_float2(x0, x1);
+              break;
+            case GEMM_CPLX_T_PLANES:
+              if (n + 1 < g.N) {
+                uint32_t p1, p2, p3;
+                tc::split_bf16x3(x0, x1, p1, p2, p3);
+                const int64_t w = ((int64_t)(n >> 1) * g.ldp + 2 * m) >> 1;
+                reinterpret_cast<uint32_t*>(g.outp[0])[w] = p1;
+                reinterpret_cast<uint32_t*>(g.outp[1])[w] = p2;
+                reinterpret_cast<uint32_t*>(g.outp[2])[w] = p3;
+              }
+              break;
+            default: break;
+          }
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tc::smem_u32(&s_acce[a]));
+    }
   }
+  if (!ok && g.status) atomicCAS(g.status, 0, (int)FS_ERR_TIMEOUT);
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc::fence_after();
-    tc::tmem_dealloc(tm, BN);
+    tc::tmem_dealloc(tm, 2 * BN);
   }
 }
 
@@ -214,14 +231,35 @@ void gemm_tc(const GemmTc& g, cudaStream_t st) {
   FS_REQUIRE(g.M > 0 && g.N > 0 && g.K > 0, FS_ERR_ARG, "empty GEMM");
   FS_REQUIRE(g.lda % 8 == 0 && g.ldb % 8 == 0, FS_ERR_ARG,
              "GEMM operand rows must be 16-byte aligned");
+  for (int p = 0; p < 3; ++p)
+    FS_REQUIRE(((uintptr_t)g.A[p] & 15) == 0 && ((uintptr_t)g.B[p] & 15) == 0, FS_ERR_ARG,
+               "GEMM operand planes must be 16-byte aligned");
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
     FS_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  gtc::SMEM));
+    int dev = 0;
+    FS_CUDA(cudaGetDevice(&dev));
+    FS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
-  dim3 grid((unsigned)((g.N + gtc::BN - 1) / gtc::BN), (unsigned)((g.M + gtc::BM - 1) / gtc::BM));
-  k_gemm_tc<<<grid, gtc::THREADS, gtc::SMEM, st>>>(g);
+  GemmMaps maps;
+  for (int p = 0; p < 3; ++p) {
+    CUresult r = tc::encode_map_2d(&maps.a[p], CU_TENSOR_MAP_DATA_TYPE_UINT16, (void*)g.A[p],
+                                   (uint64_t)g.K, (uint64_t)g.M, (uint64_t)g.lda * 2, gtc::BK,
+                                   gtc::BM, CU_TENSOR_MAP_SWIZZLE_64B);
+    FS_REQUIRE(r == CUDA_SUCCESS, FS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a GEMM operand");
+    r = tc::encode_map_2d(&maps.b[p], CU_TENSOR_MAP_DATA_TYPE_UINT16, (void*)g.B[p],
+                          (uint64_t)g.K, (uint64_t)g.N, (uint64_t)g.ldb * 2, gtc::BK, gtc::BN,
+                          CU_TENSOR_MAP_SWIZZLE_64B);
+    FS_REQUIRE(r == CUDA_SUCCESS, FS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a GEMM operand");
+  }
+  const int tiles_m = (g.M + gtc::BM - 1) / gtc::BM;
+  const int64_t tiles = (int64_t)tiles_m * ((g.N + gtc::BN - 1) / gtc::BN);
+  FS_REQUIRE(tiles <= 0x7FFFFFFF, FS_ERR_UNSUPPORTED, "GEMM too large");
+  const int grid = (int)std::min<int64_t>(tiles, sms);
+  k_gemm_tc<<<grid, gtc::THREADS, gtc::SMEM, st>>>(maps, g, tiles_m, (int)tiles);
   FS_CUDA(cudaGetLastError());
 }
 

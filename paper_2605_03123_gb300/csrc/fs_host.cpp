@@ -11,14 +11,23 @@
 namespace fs {
 
 void mat_mul(int n, const zd* A, const zd* B, zd* C) {
-  std::vector<zd> t((size_t)n * n, zd(0));
+  // real arithmetic on the parts (std::complex products carry inf/nan
+  // recovery calls that make these small products several times slower)
+  std::vector<double> t((size_t)2 * n * n, 0.0);
+  const double* a = reinterpret_cast<const double*>(A);
+  const double* b = reinterpret_cast<const double*>(B);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
-      zd a = A[i * n + k];
-      if (a == zd(0)) continue;
-      for (int j = 0; j < n; ++j) t[i * n + j] += a * B[k * n + j];
+      const double ar = a[2 * (i * n + k)], ai = a[2 * (i * n + k) + 1];
+      if (ar == 0.0 && ai == 0.0) continue;
+      double* ti = t.data() + (size_t)2 * i * n;
+      const double* bk = b + (size_t)2 * k * n;
+      for (int j = 0; j < n; ++j) {
+        ti[2 * j] += ar * bk[2 * j] - ai * bk[2 * j + 1];
+        ti[2 * j + 1] += ar * bk[2 * j + 1] + ai * bk[2 * j];
+      }
     }
-  std::copy(t.begin(), t.end(), C);
+  std::copy(t.begin(), t.end(), reinterpret_cast<double*>(C));
 }
 
 void mat_adjoint(int n, const zd* A, zd* out) {

@@ -310,11 +310,13 @@ void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& 
 
 // Window program: step s applies Givens g0[s] .. g0[s+1]-1, all acting on
 // orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
-// index of the rotated pair (p, p+1).
+// index of the rotated pair (p, p+1); pat[s] >= 0 names the step's
+// u-sequence among the compile-time window patterns (-1: none).
 template <typename R>
 struct WProg {
   int nsteps;
   int8_t a[kMaxGivens];
+  int8_t pat[kMaxGivens];
   int16_t g0[kMaxGivens + 1];
   int8_t u[kMaxGivens];
   R c[kMaxGivens];

@@ -87,20 +87,6 @@ __global__ void k_dc_ypieces(__nv_bfloat16* y, float2* eab, const uint32_t* mb, 
   eab[j] = j < db ? (eb ? eb[j] : make_float2(1.f, 0.f)) : make_float2(0.f, 0.f);
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
-               ::"l"(map), "r"(x), "r"(y), "r"(src)
-               : "memory");
-}
-
 template <int NK>
 __global__ void __launch_bounds__(dct::THREADS, 1)
     k_phase_tc(const __grid_constant__ CUtensorMap map, const __nv_bfloat16* occ,
@@ -142,7 +128,7 @@ __global__ void __launch_bounds__(dct::THREADS, 1)
     const uint32_t st = sbase + (uint32_t)(s * SSTRIDE);
     const uint32_t mb = tc::smem_u32(&s_full[s]);
     tc::mbar_expect_tx(mb, (uint32_t)SB);
-    tma_load_2d(st, &map, (int)(tj * TJ), (int)(ti * TI), mb);
+    tc::tma_load_2d(st, &map, (int)(tj * TJ), (int)(ti * TI), mb);
     tc::bulk_g2s(st + OFF_OCC, occ + ti * (occ_bytes(NK) / 2), occ_bytes(NK), mb);
     tc::bulk_g2s(st + OFF_Y, ypc + tj * (y_bytes(NK) / 2), y_bytes(NK), mb);
     tc::bulk_g2s(st + OFF_EA, eaa + ti * TI, TI * 8, mb);
@@ -233,7 +219,7 @@ __global__ void __launch_bounds__(dct::THREADS, 1)
     if (tid == 0) {
       const int64_t t = blockIdx.x + u * gridDim.x;
       const int64_t ti = t / ntj, tj = t - ti * ntj;
-      tma_store_2d(&map, (int)(tj * TJ), (int)(ti * TI), st);
+      tc::tma_store_2d(&map, (int)(tj * TJ), (int)(ti * TI), st);
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
@@ -270,6 +256,18 @@ static EncodeTiled encode_tiled() {
     fn = (EncodeTiled)p;
   }
   return fn;
+}
+
+CUresult tc::encode_map_2d(CUtensorMap* map, CUtensorMapDataType type, void* base, uint64_t inner,
+                          uint64_t outer, uint64_t row_bytes, uint32_t box_inner,
+                          uint32_t box_outer, CUtensorMapSwizzle swizzle) {
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode_tiled()(map, type, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 void launch_phase_tc(Ctx* ctx, const Space* sa, const Space* sb, void* vec, const PhaseDev& ph,

@@ -27,6 +27,7 @@
 //   * each thread reads its lane of D back and scatters the new amplitudes
 //     to the slab.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,6 +90,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
 // Bounded wait for phase `parity` of an mbarrier: about one second of
 // clock cycles at most; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
@@ -113,6 +117,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
       : "memory");
+}
+// 2-D TMA tile load global -> shared, completing on the mbarrier; x is the
+// inner (contiguous) coordinate, x * element size a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+// 2-D TMA tile store shared -> global (bulk group of the issuing thread);
+// x, y must not be negative.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(map), "r"(x), "r"(y), "r"(src)
+               : "memory");
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -189,6 +210,13 @@ __device__ __forceinline__ void split_bf16x3(float re, float im, uint32_t& p1, u
   p2 = __byte_perm(ur1, ui1, 0x7632);
   p3 = __byte_perm(__float_as_uint(r2), __float_as_uint(i2), 0x7632);
 }
+
+// Host: a 2-D tensor map (inner extent x outer extent elements, rows
+// row_bytes apart, boxes box_inner x box_outer) through the driver's
+// cuTensorMapEncodeTiled; out-of-range elements of a box read as zeros.
+CUresult encode_map_2d(CUtensorMap* map, CUtensorMapDataType type, void* base, uint64_t inner,
+                       uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                       CUtensorMapSwizzle swizzle);
 
 }  // namespace tc
 }  // namespace fs
