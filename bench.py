@@ -51,7 +51,7 @@ def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2605_03123_gb300", "csrc", "fs_sweep.cu")
+    src = os.path.join(ROOT, "paper_2605_03123_gb300", "csrc", "fs_sweep_kern.cuh")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
@@ -709,6 +709,76 @@ def run_operator_action(args, ctx):
     return res
 
 
+def run_host_copies(args, ctx):
+    """Diagnostics of the end-to-end leg (not part of the default run): the
+    time of one 1.33 GB pinned host-to-device copy of the N=16 state when
+    copies run back to back, right after an N=16 forward pass, after idle
+    pauses of 0.01-2 s, and concurrently with a forward pass (which is timed
+    too); and one device-to-host copy."""
+    import torch
+    from paper_2605_03123_gb300 import fsgpu
+    w = workload(None)
+    K, Jaa, Jab = w["K"], w["J_aa"], w["J_ab"]
+    hv = torch.empty(w["vec"].shape, dtype=torch.complex64, pin_memory=True)
+    hv.copy_(torch.from_numpy(w["vec"].astype(np.complex64)))
+    dv = torch.empty(hv.shape, dtype=torch.complex64, device="cuda")
+    dw = dv.clone()
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+
+    def copy_ms(dst, src, stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        return e0, e1
+
+    def fwd():
+        fsgpu.lucj_forward_(dw, K, Jaa, Jab, NORB, NELEC, ctx=ctx)
+
+    def el(e):
+        return e[0].elapsed_time(e[1])
+
+    fwd()
+    torch.cuda.synchronize()
+    out = {"bytes": hv.numel() * 8, "unit": "ms"}
+    r = []
+    for _ in range(4):
+        e = copy_ms(dv, hv, main)
+        torch.cuda.synchronize()
+        r.append(el(e))
+    out["h2d_back_to_back"] = r
+    e = copy_ms(hv, dv, main)
+    torch.cuda.synchronize()
+    out["d2h_after_copies"] = el(e)
+    for pause in (0.0, 0.01, 0.1, 0.5, 2.0):
+        fwd()
+        torch.cuda.synchronize()
+        time.sleep(pause)
+        e = copy_ms(dv, hv, main)
+        torch.cuda.synchronize()
+        out["h2d_after_forward_and_%gs_idle" % pause] = el(e)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(main)
+    fwd()
+    f1.record(main)
+    torch.cuda.synchronize()
+    out["forward_alone"] = f0.elapsed_time(f1)
+    time.sleep(0.5)
+    f0.record(main)
+    fwd()
+    f1.record(main)
+    e = copy_ms(dv, hv, side)
+    torch.cuda.synchronize()
+    out["h2d_during_forward_after_0.5s_idle"] = el(e)
+    out["forward_during_that_copy"] = f0.elapsed_time(f1)
+    return out
+
+
+SECTIONS = {}
+
+
 def run_sampling_only(args):
     """Profiling only: the sampling section alone, at the sector given by
     --norb/--nalpha/--nbeta (default the N=16 (8,8) workload)."""
@@ -999,7 +1069,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fsgpu", choices=["fsgpu", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--c128-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=2,
@@ -1020,14 +1090,27 @@ def main():
                     help="shots per call of the state-sampling section")
     ap.add_argument("--sampling-only", action="store_true",
                     help="profiling only: the sampling section alone")
+    ap.add_argument("--section", choices=sorted(SECTIONS),
+                    help="profiling only: one of the extra sections alone")
     args = ap.parse_args()
     if args.sampling_only:
         run_sampling_only(args)
+    elif args.section:
+        from paper_2605_03123_gb300 import fsgpu
+        fsgpu.load_library()
+        print(json.dumps({args.section: SECTIONS[args.section](args, fsgpu.context(0))}))
     elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
 
+
+SECTIONS.update({"dc_phase": lambda a, c: run_dc_phase(a, c),
+                 "small_rotation": lambda a, c: run_small_rotation(a, c),
+                 "trotter": lambda a, c: run_trotter(a, c),
+                 "operator_action": lambda a, c: run_operator_action(a, c),
+                 "sampling": lambda a, c: run_sampling(a, c),
+                 "host_copies": lambda a, c: run_host_copies(a, c)})
 
 if __name__ == "__main__":
     main()

@@ -122,7 +122,8 @@ int fs_set_sweep_engine(fs_ctx *ctx, int engine);
 /* Autotuner of the batched LUCJ sweeps (fs_lucj_batch): on the first call
  * that meets a sector (norb, electrons of both spins), precision and sweep
  * kind, every slab width (vectors per CTA, 1 .. 64 within the stage's
- * shared-memory budget) is timed as a one-circuit launch of the batched
+ * shared-memory budget; at least 2 for complex64 forward sweeps, which run
+ * on packed vector pairs) is timed as a one-circuit launch of the batched
  * kernel on scratch states, before the batch is captured, and the fastest
  * is kept for the context.  on = 0 switches it off (and forgets the choices;
  * untuned batches use about eight slabs per circuit); on = 1 (the default)
@@ -130,7 +131,8 @@ int fs_set_sweep_engine(fs_ctx *ctx, int engine);
 int fs_set_batch_tuning(fs_ctx *ctx, int on);
 /* The autotuner's choices as JSON, NUL terminated, into out[0..cap):
  * [{"norb", "n_this", "n_other", "dtype", "states", "reverse", "cross",
- *   "budget_kb", "vectors_per_cta", "ms": [per slab width 1, 2, 4, ...]}].
+ *   "budget_kb", "vectors_per_cta", "widths": [the timed slab widths],
+ *   "ms": [the time of each]}].
  * FS_ERR_ARG if it does not fit. */
 int fs_tuning_report(fs_ctx *ctx, char *out, int64_t cap);
 

@@ -585,12 +585,18 @@ int fs_tuning_report(fs_ctx* ctx, char* out, int64_t cap) {
             ",\"n_other\":" + std::to_string(k[2]) + ",\"dtype\":" + std::to_string(k[3]) +
             ",\"states\":" + std::to_string(k[4]) + ",\"reverse\":" + std::to_string(k[5]) +
             ",\"cross\":" + std::to_string(k[6]) + ",\"budget_kb\":" + std::to_string(k[7]) +
-            ",\"vectors_per_cta\":" + std::to_string(1 << kv.second) + ",\"ms\":[";
+            ",\"vectors_per_cta\":" + std::to_string(1 << kv.second);
+      // the timed widths (a zero time marks a width that was not a candidate)
+      std::string w = ",\"widths\":[", t = ",\"ms\":[";
       const auto m = ctx->sweep_tune_ms.find(k);
       if (m != ctx->sweep_tune_ms.end())
-        for (size_t i = 0; i < m->second.size(); ++i)
-          js += (i ? "," : "") + std::to_string(m->second[i]);
-      js += "]}";
+        for (size_t i = 0, n = 0; i < m->second.size(); ++i) {
+          if (!(m->second[i] > 0.f)) continue;
+          w += (n ? "," : "") + std::to_string(1 << i);
+          t += (n ? "," : "") + std::to_string(m->second[i]);
+          ++n;
+        }
+      js += w + "]" + t + "]}";
     }
     js += "]";
     FS_REQUIRE((int64_t)js.size() < cap, FS_ERR_ARG, "report buffer too small");

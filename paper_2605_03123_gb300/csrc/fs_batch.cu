@@ -312,6 +312,7 @@ struct Stage {
   int64_t total = 0, total2 = 0, total3 = 0;
   size_t smem = 0;
   int counter = -1;
+  bool pk = false;
 };
 
 }  // namespace
@@ -491,6 +492,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     S.nst = nst;
     int64_t items = 0;
     size_t smem = 0;
+    bool pk = true;
     const size_t budget = nst == 1 ? half_sm : maxsm;
     for (auto& C : cs) {
       if (!use(C)) continue;
@@ -509,6 +511,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
       j.item0 = (int)items;
       items += plan.nslabs;
       smem = std::max(smem, plan.smem);
+      pk = pk && plan.pk;
       P.jobs.push_back(j);
       P.prog_off.push_back(img.add(plan.prog.data(), plan.prog.size()));
       P.x_off.push_back(xk >= 0 ? C.xab_off + (size_t)xk * sizeof(Mat) : (size_t)-1);
@@ -518,6 +521,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
     S.njobs = (int)P.jobs.size();
     S.total = items;
     S.smem = smem;
+    S.pk = pk;
     stages.push_back(S);
     pend.push_back(std::move(P));
   };
@@ -755,7 +759,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
 
   // kernel attributes are set before the capture starts
   for (auto& S : stages)
-    if (S.kind == 1) launch_sweep_batch(ctx, dtype, S.nst, nullptr, 0, 0, nullptr, S.smem, st);
+    if (S.kind == 1) launch_sweep_batch(ctx, dtype, S.nst, nullptr, 0, 0, nullptr, S.smem, st, S.pk);
   // ---- record the stages into one graph and launch it on `st`
   if (!ctx->capture_stream)
     FS_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
@@ -783,7 +787,7 @@ static void lucj_batch_impl(Ctx* ctx, int n, const fs_lucj* ops, void* const* ve
           k_hf_batch<double><<<grid, 256, 0, cst>>>((const BVec*)jp, S.njobs, S.total);
       } else if (S.kind == 1) {
         launch_sweep_batch(ctx, dtype, S.nst, (const SweepJob*)jp, S.njobs, (int)S.total,
-                           counters + S.counter, S.smem, cst);
+                           counters + S.counter, S.smem, cst, S.pk);
       } else if (S.kind == 4) {
         unsigned grid = (unsigned)std::min<int64_t>((S.total + 63) / 64, 16 * sms);
         k_slater_batch<<<grid, 64, 0, cst>>>((const BSl*)jp, S.njobs, S.total);

@@ -91,10 +91,13 @@ struct TcSeg {
 };
 
 // Device copy of a pass: the subset, the owned slots, the record range.
+// mode: 2 = the pass owns all 16 local slots, 1 = all twelve off-diagonal
+// slots and no diagonal, 0 = any other ownership (tested per slot).
 struct TPassDev {
   int q[4];
   uint32_t keep;
   int rec0, rec1;
+  int mode;
 };
 // Transition-reduction passes (see tpass_tables_host): a subset of four
 // orbitals q[0] < .. < q[3], the local slots (i*4 + j <-> E_{q_i q_j}) this
@@ -312,16 +315,49 @@ void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& 
 // orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
 // index of the rotated pair (p, p+1); pat[s] >= 0 names the step's
 // u-sequence among the compile-time window patterns (-1: none).
+// Coefficients c, Re s, Im s of each rotation: complex128 keeps them as
+// doubles; complex64 keeps each as a pair (x, x) (and -Re s, -Im s as
+// pairs) for the packed two-lane FP32 updates, read as floats elsewhere.
 template <typename R>
-struct WProg {
+struct WCoef {
+  R c[kMaxGivens];
+  R sr[kMaxGivens];
+  R si[kMaxGivens];
+  __host__ __device__ R cf(int q) const { return c[q]; }
+  __host__ __device__ R srf(int q) const { return sr[q]; }
+  __host__ __device__ R sif(int q) const { return si[q]; }
+  __host__ void set(int q, double cv, double srv, double siv) {
+    c[q] = (R)cv;
+    sr[q] = (R)srv;
+    si[q] = (R)siv;
+  }
+};
+template <>
+struct WCoef<float> {
+  float2 c2[kMaxGivens];
+  float2 sr2[kMaxGivens];
+  float2 si2[kMaxGivens];
+  float2 nsr2[kMaxGivens];
+  float2 nsi2[kMaxGivens];
+  __host__ __device__ float cf(int q) const { return c2[q].x; }
+  __host__ __device__ float srf(int q) const { return sr2[q].x; }
+  __host__ __device__ float sif(int q) const { return si2[q].x; }
+  __host__ void set(int q, double cv, double srv, double siv) {
+    const float c = (float)cv, sr = (float)srv, si = (float)siv;
+    c2[q] = make_float2(c, c);
+    sr2[q] = make_float2(sr, sr);
+    si2[q] = make_float2(si, si);
+    nsr2[q] = make_float2(-sr, -sr);
+    nsi2[q] = make_float2(-si, -si);
+  }
+};
+template <typename R>
+struct WProg : WCoef<R> {
   int nsteps;
   int8_t a[kMaxGivens];
   int8_t pat[kMaxGivens];
   int16_t g0[kMaxGivens + 1];
   int8_t u[kMaxGivens];
-  R c[kMaxGivens];
-  R sr[kMaxGivens];
-  R si[kMaxGivens];
 };
 
 // Geometry and phase/reduction pointers of one sweep launch (one job of a
@@ -398,6 +434,7 @@ struct BatchSweepPlan {
   SweepGeom g;
   int nslabs = 0;
   size_t smem = 0;
+  bool pk = false;                  // packed vector pairs (complex64 forward)
   std::vector<unsigned char> prog;  // WProg<R> bytes
 };
 size_t wprog_bytes(int dtype);
@@ -405,8 +442,10 @@ void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* 
                       int dtype, const RotProgram& rp, const PhaseDev& ph, const struct RevArgs* rev,
                       size_t budget, BatchSweepPlan& out);
 // jobs == nullptr: only set the kernel's shared-memory attribute.
+// pk: every job's slab holds an even number of vectors (complex64 forward
+// sweeps then run on packed vector pairs)
 void launch_sweep_batch(Ctx* ctx, int dtype, int nst, const SweepJob* jobs, int njobs, int total,
-                        int* counter, size_t smem, cudaStream_t st);
+                        int* counter, size_t smem, cudaStream_t st, bool pk = false);
 void lucj_batch(Ctx* ctx, int n, const fs_lucj* ops, void* const* vecs, void* const* cots,
                 int dtype, int do_vjp, double* const* dK, double* const* dJaa,
                 double* const* dJab, cudaStream_t st);

@@ -18,7 +18,11 @@ extern template void dispatch_cs<float, 1, false, 6, 256, WProg<float>, false>(
     int, const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
 extern template void dispatch_cs<float, 1, false, 6, 512, WProg<float>, false>(
     int, const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
-extern template void launch_sweep_t<float, 1, 2, true, 6, 512, true, WProg<float>, false>(
+extern template void launch_sweep_t<float, 1, 1, false, 6, 256, false, WProg<float>, false, true>(
+    const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
+extern template void launch_sweep_t<float, 1, 1, false, 6, 512, false, WProg<float>, false, true>(
+    const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
+extern template void launch_sweep_t<float, 1, 2, true, 6, 512, false, WProg<float>, false, true>(
     const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
 extern template void dispatch_cs<float, 2, true, 5, 512, WProg<float>, false>(
     int, const SweepGeom&, const WProg<float>&, const Mat&, int, size_t, cudaStream_t);
@@ -26,7 +30,11 @@ extern template void launch_batch_t<float, 1, false, 6, 256, false>(const SweepJ
                                                                    size_t, int, cudaStream_t);
 extern template void launch_batch_t<float, 1, false, 6, 512, false>(const SweepJob*, int, int, int*,
                                                                    size_t, int, cudaStream_t);
-extern template void launch_batch_t<float, 2, true, 6, 512, true>(const SweepJob*, int, int, int*,
+extern template void launch_batch_t<float, 1, false, 6, 256, false, true>(const SweepJob*, int, int, int*,
+                                                                         size_t, int, cudaStream_t);
+extern template void launch_batch_t<float, 1, false, 6, 512, false, true>(const SweepJob*, int, int, int*,
+                                                                         size_t, int, cudaStream_t);
+extern template void launch_batch_t<float, 2, true, 6, 512, false, true>(const SweepJob*, int, int, int*,
                                                                  size_t, int, cudaStream_t);
 
 // The B images of the tensor-core steps of one program, FP64 on the device:
@@ -142,6 +150,8 @@ static void build_tpass_tables(Space* sp) {
     pd[i].keep = passes[i].keep;
     pd[i].rec0 = passes[i].rec0;
     pd[i].rec1 = passes[i].rec1;
+    const uint32_t diag = 0x8421u, all = 0xFFFFu;
+    pd[i].mode = passes[i].keep == all ? 2 : passes[i].keep == (all & ~diag) ? 1 : 0;
   }
   if (!pd.empty()) {
     FS_CUDA(cudaMalloc(&sp->tpass, pd.size() * sizeof(TPassDev)));
@@ -247,9 +257,7 @@ static WProg<R> make_wprog(const RotProgram& rp, int N, int W) {
     w.pat[st] = (int8_t)match_pattern(W, useq_host);
     for (int k : steps[st].givens) {
       w.u[ng] = (int8_t)(rp.g[k].p - steps[st].a);
-      w.c[ng] = (R)rp.g[k].c;
-      w.sr[ng] = (R)rp.g[k].s.real();
-      w.si[ng] = (R)rp.g[k].s.imag();
+      w.set(ng, rp.g[k].c, rp.g[k].s.real(), rp.g[k].s.imag());
       ++ng;
     }
   }
@@ -287,10 +295,10 @@ static void set_window_geom(SweepGeom& g, Space* sp, int W) {
 
 // Kernel choice: window sweeps when the orbitals allow a window; forward
 // sweeps on 256 threads when a slab is small enough for two CTAs per SM
-// (their window-step barriers then overlap), else 512; reverse sweeps in
-// split mode (one half-CTA per state) unless the vector spans a cluster (in a
-// cluster the joint form measured faster: the split form gains little when
-// every step ends on the cluster barrier).
+// (their window-step barriers then overlap), else 512; reverse sweeps with
+// both states of an orbit in one thread (complex64 in one CTA: W = 6;
+// clusters: W = 5), complex128 in one CTA in split mode (one half-CTA per
+// state, W = 5).
 // Gather indices of the tensor-core steps (see TcSeg), built once per space:
 // b = 0 for the whole orbit list of each window position, b = 1 for the two
 // rank groups of 2-CTA blocked clusters.  Row o of class m holds the
@@ -397,6 +405,18 @@ static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotPr
       SweepGeom g = g0;
       set_window_geom(g, sthis, W);
       auto prog = make_wprog<R>(rp, sthis->norb, W);
+      if constexpr (sizeof(R) == 4) {
+        // slabs of an even number of vectors: packed vector pairs
+        if (CS == 1 && g.lgKV >= 1) {
+          if (two_per_sm)
+            launch_sweep_t<R, 1, 1, false, W, 256, false, WProg<R>, false, true>(g, prog, X,
+                                                                               nslabs, smem, st);
+          else
+            launch_sweep_t<R, 1, 1, false, W, 512, false, WProg<R>, false, true>(g, prog, X,
+                                                                               nslabs, smem, st);
+          return;
+        }
+      }
       if (two_per_sm)
         dispatch_cs<R, NST, VJP, W, 256>(CS, g, prog, X, nslabs, smem, st);
       else
@@ -410,7 +430,13 @@ static void dispatch_prog(Space* sthis, int CS, const SweepGeom& g0, const RotPr
       SweepGeom g = g0;
       set_window_geom(g, sthis, WS);
       auto prog = make_wprog<R>(rp, sthis->norb, WS);
-      launch_sweep_t<R, 1, NST, VJP, WS, 512, true>(g, prog, X, nslabs, smem, st);
+      if constexpr (sizeof(R) == 4)
+        // complex64: psi and g of an orbit in one thread, packed per string
+        // (W = 6; shared addresses and coefficients, two-lane updates)
+        launch_sweep_t<R, 1, NST, VJP, WS, 512, false, WProg<R>, false, true>(g, prog, X, nslabs,
+                                                                              smem, st);
+      else
+        launch_sweep_t<R, 1, NST, VJP, WS, 512, true>(g, prog, X, nslabs, smem, st);
       return;
     }
     if (sthis->norb >= WJ && sthis->dim > 1) {
@@ -556,12 +582,19 @@ void launch_sweep(Ctx* ctx, const Space* sa, const Space* sb, int dir, void* st0
   FS_REQUIRE(CS <= 8, FS_ERR_UNSUPPORTED, "state vector too large for a cluster of 8");
   // two CTAs per SM for single-state sweeps whose slab fits half the SM
   const size_t half_sm = (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 - 1024;
-  const bool two_per_sm = nst == 1 && CS == 1 && smem_for(1, 1) <= half_sm;
+  bool two_per_sm = nst == 1 && CS == 1 && smem_for(1, 1) <= half_sm;
+  // complex64 forward sweeps work on packed vector pairs: when only one
+  // vector would fit half an SM but two fit the whole, one CTA of 512
+  // threads per SM holding two vectors beats two CTAs holding one each
+  const bool pair_slab = dtype == FS_C64 && nst == 1 && CS == 1 && g.nvec >= 2 &&
+                         smem_for(1, 2) > half_sm && smem_for(1, 2) <= maxsm;
+  if (pair_slab) two_per_sm = false;
   const size_t budget = two_per_sm ? half_sm : maxsm;
   // vectors per slab: fit the budget, keep >= 2 slabs per SM when possible
   int want = std::max(1, g.nvec / (2 * ctx->prop.multiProcessorCount));
   int lg = 0;
   while ((2 << lg) <= std::min(want, kMaxKV) && smem_for(CS, 2 << lg) <= budget) ++lg;
+  if (pair_slab && lg == 0) lg = 1;
   g.lgKV = lg;
   set_cluster_layout(g, sthis, CS, [&](int chunk) {
     return (size_t)(chunk * csz * nst + tab_per_kv + fixed) + tsum <= maxsm;
@@ -606,8 +639,8 @@ int batch_window(int dtype, int nst) {
 // sweep kind.  Runs before any capture.
 template <typename SmemFor>
 static int tune_batch_slab(Ctx* ctx, const SweepGeom& g0, const std::vector<unsigned char>& prog,
-                           int nst, int dtype, bool rev, int lgmax, SmemFor&& smem_for,
-                           const std::array<int, 8>& key) {
+                           int nst, int dtype, bool rev, int lgmin, int lgmax,
+                           SmemFor&& smem_for, const std::array<int, 8>& key) {
   if (!ctx->tune_stream)
     FS_CUDA(cudaStreamCreateWithFlags(&ctx->tune_stream, cudaStreamNonBlocking));
   cudaStream_t ts = ctx->tune_stream;
@@ -634,8 +667,8 @@ static int tune_batch_slab(Ctx* ctx, const SweepGeom& g0, const std::vector<unsi
   FS_CUDA(cudaEventCreate(&e0));
   FS_CUDA(cudaEventCreate(&e1));
   std::vector<float> ms(lgmax + 1, 0.f);
-  int best = 0;
-  for (int lg = 0; lg <= lgmax; ++lg) {
+  int best = lgmin;
+  for (int lg = lgmin; lg <= lgmax; ++lg) {
     g.lgKV = lg;
     SweepJob j{};
     j.g = g;
@@ -645,12 +678,13 @@ static int tune_batch_slab(Ctx* ctx, const SweepGeom& g0, const std::vector<unsi
     const int nslabs = (g.nvec + (1 << lg) - 1) >> lg;
     const size_t smem = smem_for(1 << lg);
     FS_CUDA(cudaMemcpyAsync(djob, &j, sizeof(j), cudaMemcpyHostToDevice, ts));
-    launch_sweep_batch(ctx, dtype, nst, nullptr, 0, 0, nullptr, smem, ts);  // attribute
+    const bool pk = lgmin > 0;
+    launch_sweep_batch(ctx, dtype, nst, nullptr, 0, 0, nullptr, smem, ts, pk);  // attribute
     float tot = 0;
     for (int r = 0; r < 3; ++r) {
       FS_CUDA(cudaMemsetAsync(dcounter, 0, sizeof(int), ts));
       if (r == 1) FS_CUDA(cudaEventRecord(e0, ts));
-      launch_sweep_batch(ctx, dtype, nst, djob, 1, nslabs, dcounter, smem, ts);
+      launch_sweep_batch(ctx, dtype, nst, djob, 1, nslabs, dcounter, smem, ts, pk);
     }
     FS_CUDA(cudaEventRecord(e1, ts));
     FS_CUDA(cudaEventSynchronize(e1));
@@ -724,38 +758,50 @@ void plan_batch_sweep(Ctx* ctx, Space* sa, Space* sb, int dir, void* st0, void* 
   // autotuned width for this sector and sweep kind
   int lgmax = 0;
   while ((2 << lgmax) <= std::min(g.nvec, kMaxKV) && smem_for(2 << lgmax) <= budget) ++lgmax;
+  // complex64 forward sweeps: at least two vectors per slab, run as packed
+  // vector pairs
+  const int lgmin = dtype == FS_C64 && nst == 1 && lgmax >= 1 ? 1 : 0;
   const std::array<int, 8> key = {sthis->norb, sthis->nocc, sother->nocc, dtype, nst,
                                   rev != nullptr, ph.has_x, (int)(budget >> 10)};
   int lg = -1;
   auto it = ctx->sweep_tune.find(key);
   if (it != ctx->sweep_tune.end()) {
     lg = std::min(it->second, lgmax);
-  } else if (ctx->batch_tuning && lgmax > 0) {
-    lg = tune_batch_slab(ctx, g, out.prog, nst, dtype, rev != nullptr, lgmax, smem_for, key);
+  } else if (ctx->batch_tuning && lgmax > lgmin) {
+    lg = tune_batch_slab(ctx, g, out.prog, nst, dtype, rev != nullptr, lgmin, lgmax, smem_for,
+                         key);
   }
   if (lg < 0) {  // untuned: about eight slabs per circuit
     const int want = std::max(1, g.nvec / 8);
     lg = 0;
     while ((2 << lg) <= std::min(want, kMaxKV) && lg < lgmax) ++lg;
   }
+  lg = std::max(lg, lgmin);
   g.lgKV = lg;
   out.nslabs = (g.nvec + (1 << lg) - 1) >> lg;
   out.smem = smem_for(1 << lg);
+  out.pk = lgmin > 0;
 }
 
 void launch_sweep_batch(Ctx* ctx, int dtype, int nst, const SweepJob* jobs, int njobs, int total,
-                        int* counter, size_t smem, cudaStream_t st) {
+                        int* counter, size_t smem, cudaStream_t st, bool pk) {
   const int sms = ctx->prop.multiProcessorCount;
   const size_t half_sm = (size_t)ctx->prop.sharedMemPerMultiprocessor / 2 - 1024;
   if (dtype == FS_C64) {
     constexpr int W = window_width<float, 1>();
-    if (nst == 1) {
+    if (nst == 1 && pk) {
+      if (smem <= half_sm)
+        launch_batch_t<float, 1, false, W, 256, false, true>(jobs, njobs, total, counter, smem, 2 * sms, st);
+      else
+        launch_batch_t<float, 1, false, W, 512, false, true>(jobs, njobs, total, counter, smem, sms, st);
+    } else if (nst == 1) {
       if (smem <= half_sm)
         launch_batch_t<float, 1, false, W, 256, false>(jobs, njobs, total, counter, smem, 2 * sms, st);
       else
         launch_batch_t<float, 1, false, W, 512, false>(jobs, njobs, total, counter, smem, sms, st);
     } else {
-      launch_batch_t<float, 2, true, W, 512, true>(jobs, njobs, total, counter, smem, sms, st);
+      // psi and g packed per string, one thread per orbit of both
+      launch_batch_t<float, 2, true, W, 512, false, true>(jobs, njobs, total, counter, smem, sms, st);
     }
   } else {
     constexpr int W = window_width<double, 1>();

@@ -7,6 +7,10 @@ template void launch_batch_t<float, 1, false, 6, 256, false>(const SweepJob*, in
                                                             size_t, int, cudaStream_t);
 template void launch_batch_t<float, 1, false, 6, 512, false>(const SweepJob*, int, int, int*,
                                                             size_t, int, cudaStream_t);
-template void launch_batch_t<float, 2, true, 6, 512, true>(const SweepJob*, int, int, int*,
+template void launch_batch_t<float, 1, false, 6, 256, false, true>(const SweepJob*, int, int, int*,
+                                                                  size_t, int, cudaStream_t);
+template void launch_batch_t<float, 1, false, 6, 512, false, true>(const SweepJob*, int, int, int*,
+                                                                  size_t, int, cudaStream_t);
+template void launch_batch_t<float, 2, true, 6, 512, false, true>(const SweepJob*, int, int, int*,
                                                           size_t, int, cudaStream_t);
 }  // namespace fs

@@ -126,7 +126,7 @@ constexpr int win_npat() {
 template <int W, int M, typename R, int NV, int NS, int... U, int... K>
 __device__ __forceinline__ void win_seq(cx_t<R> (&v)[NV][NS], const WProg<R>& prog, int ga,
                                         useq<U...>, std::integer_sequence<int, K...>) {
-  (win_pairs<W, M, U, R, NV, NS>(v, prog.c[ga + K], prog.sr[ga + K], prog.si[ga + K]), ...);
+  (win_pairs<W, M, U, R, NV, NS>(v, prog.cf(ga + K), prog.srf(ga + K), prog.sif(ga + K)), ...);
 }
 template <int W, int M, typename R, int NV, int NS, int I>
 __device__ __forceinline__ bool win_pattern(int pid, cx_t<R> (&v)[NV][NS], const WProg<R>& prog,
@@ -417,6 +417,33 @@ __device__ void tc_window_steps(const SweepGeom& g, const WProg<float>& prog,
 }
 
 
+// The rotations ga .. gb-1 of a window step on NV register copies of an
+// orbit: through the step's compile-time pattern when it has one (PAT: the
+// complex64 single-CTA kernels on one copy; with two copies the unrolled
+// code outgrows the instruction cache and measured slower, and the other
+// kernels keep one loop to bound the build time), else one dispatch per
+// rotation.
+template <int W, int M, typename R, int NV, int NS, bool PAT>
+__device__ __forceinline__ void win_apply(cx_t<R> (&v)[NV][NS], const WProg<R>& prog, int ga,
+                                          int gb, int pid) {
+  constexpr int npat = PAT ? win_npat<W>() : 0;
+  if (win_patterns<W, M, R, NV, NS>(pid, v, prog, ga, std::make_index_sequence<(size_t)npat>{}))
+    return;
+  for (int q = ga; q < gb; ++q) {
+    const R c = prog.cf(q), sr = prog.srf(q), si = prog.sif(q);
+    switch (prog.u[q]) {
+      case 0: win_pairs<W, M, 0, R, NV, NS>(v, c, sr, si); break;
+      case 1: win_pairs<W, M, 1, R, NV, NS>(v, c, sr, si); break;
+      case 2: win_pairs<W, M, 2, R, NV, NS>(v, c, sr, si); break;
+      case 3: win_pairs<W, M, 3, R, NV, NS>(v, c, sr, si); break;
+      case 4: win_pairs<W, M, 4, R, NV, NS>(v, c, sr, si); break;
+      case 5: win_pairs<W, M, 5, R, NV, NS>(v, c, sr, si); break;
+      case 6: win_pairs<W, M, 6, R, NV, NS>(v, c, sr, si); break;
+      default: break;
+    }
+  }
+}
+
 // One orbit of a window step: the C(W, M) strings sharing the occupation
 // outside the window.  Their addresses are R_O + F[c_lo][S]; every vector of
 // the slab is rotated in registers by the step's Givens rotations.
@@ -457,29 +484,109 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
 #pragma unroll
       for (int k = 0; k < NS; ++k)
         v[x][k] = base[CS > 1 ? own[k] : 0][x * st_stride + ad[k] + kv];
-    // compile-time patterns for the complex64 single-CTA and pair-cluster
-    // kernels (the others keep one loop: it bounds the build time)
-    constexpr int npat = (sizeof(R) == 4 && CS == 1) ? win_npat<W>() : 0;
-    if (!win_patterns<W, M, R, NST, NS>(pid, v, prog, ga, std::make_index_sequence<(size_t)npat>{}))
-    for (int q = ga; q < gb; ++q) {
-      const R c = prog.c[q], sr = prog.sr[q], si = prog.si[q];
-      switch (prog.u[q]) {
-        case 0: win_pairs<W, M, 0, R, NST, NS>(v, c, sr, si); break;
-        case 1: win_pairs<W, M, 1, R, NST, NS>(v, c, sr, si); break;
-        case 2: win_pairs<W, M, 2, R, NST, NS>(v, c, sr, si); break;
-        case 3: win_pairs<W, M, 3, R, NST, NS>(v, c, sr, si); break;
-        case 4: win_pairs<W, M, 4, R, NST, NS>(v, c, sr, si); break;
-        case 5: win_pairs<W, M, 5, R, NST, NS>(v, c, sr, si); break;
-        case 6: win_pairs<W, M, 6, R, NST, NS>(v, c, sr, si); break;
-        default: break;
-      }
-    }
+    win_apply<W, M, R, NST, NS, sizeof(R) == 4 && CS == 1 && NST == 1>(v, prog, ga, gb, pid);
 #pragma unroll
     for (int x = 0; x < NST; ++x)
 #pragma unroll
       for (int k = 0; k < NS; ++k)
         base[CS > 1 ? own[k] : 0][x * st_stride + ad[k] + kv] = v[x][k];
   }
+}
+
+// ------------------------------------------- packed two-lane window steps
+// Complex64 kernels that rotate two amplitude sets under the same rotations
+// (two vectors of a slab in the forward sweeps; psi and g of one vector in
+// the reverse sweeps) keep them packed per string in a 16-byte cell
+// (Re lane 0, Re lane 1, Im lane 0, Im lane 1), so that one shared-memory
+// access moves both and each Givens update runs as packed two-lane FP32
+// (fma.rn.f32x2) with no register shuffles.  Lane 0 of cell c is at float
+// 4c, lane 1 at 4c + 1, imaginary parts 2 further.
+//
+// Packed Givens update of the pairs (x, y) of both lanes, the same
+// operations as givens2 lane by lane (so the results are bit-identical):
+//   x' = c x + s y,   y' = -s* x + c y.
+__device__ __forceinline__ void givens2_pk(float2& xr, float2& xi, float2& yr, float2& yi,
+                                           float2 c, float2 sr, float2 si, float2 nsr,
+                                           float2 nsi) {
+  const float2 xr2 = __ffma2_rn(c, xr, __ffma2_rn(sr, yr, __fmul2_rn(nsi, yi)));
+  const float2 xi2 = __ffma2_rn(c, xi, __ffma2_rn(sr, yi, __fmul2_rn(si, yr)));
+  const float2 yr2 = __ffma2_rn(c, yr, __ffma2_rn(nsr, xr, __fmul2_rn(nsi, xi)));
+  const float2 yi2 = __ffma2_rn(c, yi, __ffma2_rn(si, xr, __fmul2_rn(nsr, xi)));
+  xr = xr2;
+  xi = xi2;
+  yr = yr2;
+  yi = yi2;
+}
+template <int W, int M, int U, int J, int NS>
+__device__ __forceinline__ void win_pair_pk(float2 (&vr)[NS], float2 (&vi)[NS], const WProg<float>& prog,
+                                            int q) {
+  constexpr int sm = win_src_mask(W, M, U, J);
+  constexpr int a = win_index(W, M, sm);
+  constexpr int b = win_index(W, M, sm ^ (1 << U) ^ (1 << (U + 1)));
+  givens2_pk(vr[a], vi[a], vr[b], vi[b], prog.c2[q], prog.sr2[q], prog.si2[q], prog.nsr2[q],
+             prog.nsi2[q]);
+}
+template <int W, int M, int U, int NS, int... J>
+__device__ __forceinline__ void win_pairs_pk_seq(float2 (&vr)[NS], float2 (&vi)[NS],
+                                                 const WProg<float>& prog, int q,
+                                                 std::integer_sequence<int, J...>) {
+  (win_pair_pk<W, M, U, J, NS>(vr, vi, prog, q), ...);
+}
+template <int W, int M, int U, int NS>
+__device__ __forceinline__ void win_pairs_pk(float2 (&vr)[NS], float2 (&vi)[NS],
+                                             const WProg<float>& prog, int q) {
+  if constexpr (U + 1 < W)
+    win_pairs_pk_seq<W, M, U, NS>(vr, vi, prog, q,
+                                  std::make_integer_sequence<int, win_npairs(W, M, U)>{});
+}
+// One orbit of a window step in a packed slab, packed set kc (cell stride
+// per string KC).
+template <int W, int M>
+__device__ __forceinline__ void win_orbit_pk(uint32_t desc, const uint16_t* F, float* smf, int KC,
+                                             int kc, const WProg<float>& prog, int ga, int gb) {
+  constexpr int NS = cbinom(W, M);
+  const int RO = desc & 0xFFFF, clo = (desc >> 16) & 0xFF;
+  const uint16_t* Fc = F + (clo << W);
+  int ad[NS];
+  win_offsets<W, M>(Fc, ad, std::make_integer_sequence<int, NS>{});
+#pragma unroll
+  for (int k = 0; k < NS; ++k) ad[k] = (RO + ad[k]) * KC;
+  {
+    float2 vr[NS], vi[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(smf)[ad[k] + kc];
+      vr[k] = make_float2(t.x, t.y);
+      vi[k] = make_float2(t.z, t.w);
+    }
+    for (int q = ga; q < gb; ++q) {
+      switch (prog.u[q]) {
+        case 0: win_pairs_pk<W, M, 0, NS>(vr, vi, prog, q); break;
+        case 1: win_pairs_pk<W, M, 1, NS>(vr, vi, prog, q); break;
+        case 2: win_pairs_pk<W, M, 2, NS>(vr, vi, prog, q); break;
+        case 3: win_pairs_pk<W, M, 3, NS>(vr, vi, prog, q); break;
+        case 4: win_pairs_pk<W, M, 4, NS>(vr, vi, prog, q); break;
+        case 5: win_pairs_pk<W, M, 5, NS>(vr, vi, prog, q); break;
+        default: break;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+      reinterpret_cast<float4*>(smf)[ad[k] + kc] = make_float4(vr[k].x, vr[k].y, vi[k].x, vi[k].y);
+  }
+}
+// Float index of Re of amplitude (state s, string el, vector kv) in a
+// packed slab: one state, vector pairs (NST = 1), or psi and g (NST = 2).
+template <int NST>
+__device__ __forceinline__ size_t pk_re(int s, size_t el, int KV, int kv) {
+  if constexpr (NST == 1)
+    return 4 * (el * (size_t)(KV >> 1) + (size_t)(kv >> 1)) + (size_t)(kv & 1);
+  else
+    return 4 * (el * (size_t)KV + (size_t)kv) + (size_t)s;
+}
+__device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 
 // ------------------------------------------------ transition reduction
@@ -491,7 +598,9 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
 // amplitudes (omega(S) = prod over j in S of (-1)^{G_j}, G_j the parity of
 // O between q_0 and q_j, so omega(S) omega(S') is the O parity of the pair).
 // acc[2 (a*4 + b)], acc[2 (a*4 + b) + 1] += Re, Im of conj(g[S']) psi[S].
-template <typename R, int M, int J, int NS>
+// DIAG: the diagonal slots are evaluated; KEEP: ownership is tested per slot
+// (else every evaluated slot is owned).
+template <typename R, int M, int J, int NS, bool DIAG, bool KEEP>
 __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
                                        R (&acc)[32], uint32_t keep) {
   constexpr int k = J / 16, a = (J / 4) % 4, b = J % 4;
@@ -500,7 +609,7 @@ __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&
     constexpr int slot = a * 4 + b;
     if constexpr ((S >> b) & 1) {
       if constexpr (a == b) {
-        if (keep & (1u << slot)) {  // uniform per pass: diagonals are owned once
+        if (DIAG && (!KEEP || (keep & (1u << slot)))) {  // uniform per pass: diagonals are owned once
           acc[2 * slot] = fma(pg[k].x, ps[k].x, fma(pg[k].y, ps[k].y, acc[2 * slot]));
           acc[2 * slot + 1] = fma(pg[k].x, ps[k].y, fma(-pg[k].y, ps[k].x, acc[2 * slot + 1]));
         }
@@ -509,7 +618,7 @@ __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&
         constexpr int lo = a < b ? a : b, hi = a < b ? b : a;
         constexpr bool neg = cpopc(S & ((1 << hi) - 1) & ~((2 << lo) - 1)) & 1;
         constexpr R sg = neg ? R(-1) : R(1);
-        if (keep & (1u << slot)) {  // uniform per pass: each pair is owned once
+        if (!KEEP || (keep & (1u << slot))) {  // uniform per pass: each pair is owned once
           // acc += sg * conj(g[k2]) * psi[k], as four fused multiply-adds
           const R gx = sg * pg[k2].x, gy = sg * pg[k2].y;
           acc[2 * slot] = fma(gx, ps[k].x, fma(gy, ps[k].y, acc[2 * slot]));
@@ -519,11 +628,11 @@ __device__ __forceinline__ void t_term(const cx_t<R> (&ps)[NS], const cx_t<R> (&
     }
   }
 }
-template <typename R, int M, int NS, int... J>
+template <typename R, int M, int NS, bool DIAG, bool KEEP, int... J>
 __device__ __forceinline__ void t_terms(const cx_t<R> (&ps)[NS], const cx_t<R> (&pg)[NS],
                                         R (&acc)[32], uint32_t keep,
                                         std::integer_sequence<int, J...>) {
-  (t_term<R, M, J, NS>(ps, pg, acc, keep), ...);
+  (t_term<R, M, J, NS, DIAG, KEEP>(ps, pg, acc, keep), ...);
 }
 template <int M, int K>
 __device__ __forceinline__ int t_flip(int gb) {
@@ -539,9 +648,9 @@ __device__ __forceinline__ void t_flips(int gb, int (&fl)[sizeof...(K)],
                                         std::integer_sequence<int, K...>) {
   ((fl[K] = t_flip<M, K>(gb)), ...);
 }
-template <typename R, int CS, int M>
+template <typename R, int CS, int M, bool PK, bool DIAG = true, bool KEEP = true>
 __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base, size_t st_stride,
-                                        const int (&cbr)[CS + 1], int KV, int kv_eff,
+                                        const int (&cbr)[CS + 1], int KV, int kv0, int kv1,
                                         R (&acc)[32], uint32_t keep) {
   using C = cx_t<R>;
   constexpr int NS = cbinom(4, M);
@@ -565,13 +674,20 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
   }
   int fl[NS];
   t_flips<M>(rc.gbits, fl, std::make_integer_sequence<int, NS>{});
-  for (int kv = 0; kv < kv_eff; ++kv) {
+  for (int kv = kv0; kv < kv1; ++kv) {
     C ps[NS], pg[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      C* b0 = base[CS > 1 ? own[k] : 0];
-      ps[k] = b0[ad[k] + kv];
-      pg[k] = b0[st_stride + ad[k] + kv];
+      if constexpr (PK) {
+        // packed cell (Re psi, Re g, Im psi, Im g)
+        const float4 t = reinterpret_cast<const float4*>(base[0])[ad[k] + kv];
+        ps[k] = mk<R>(t.x, t.z);
+        pg[k] = mk<R>(t.y, t.w);
+      } else {
+        C* b0 = base[CS > 1 ? own[k] : 0];
+        ps[k] = b0[ad[k] + kv];
+        pg[k] = b0[st_stride + ad[k] + kv];
+      }
       if (fl[k]) {
         ps[k].x = -ps[k].x;
         ps[k].y = -ps[k].y;
@@ -579,7 +695,7 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
         pg[k].y = -pg[k].y;
       }
     }
-    t_terms<R, M, NS>(ps, pg, acc, keep, std::make_integer_sequence<int, 6 * 16>{});
+    t_terms<R, M, NS, DIAG, KEEP>(ps, pg, acc, keep, std::make_integer_sequence<int, 6 * 16>{});
   }
 }
 
@@ -690,12 +806,14 @@ __device__ __forceinline__ cx_t<R> ld_ea(const void* p, int64_t i) {
 // phase the first half of the CTA rotates state 0 and the second half state
 // 1, each half synchronising on its own named barrier.
 template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P,
-          bool TC = false>
+          bool TC = false, bool PK = false>
 __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, const Mat& X,
                                            const int slab, const int rank,
                                            unsigned char* smraw) {
   static_assert(!VJP || NST == 2, "reverse mode carries two states");
   static_assert(!SPLIT || (NST == 2 && W > 0), "split mode: two states, window sweeps");
+  static_assert(!PK || (CS == 1 && sizeof(R) == 4 && W > 0 && !SPLIT && !TC),
+                "packed slabs: complex64 window sweeps in one CTA");
   constexpr int kThreads = NT;
   using C = cx_t<R>;
   C* sm = reinterpret_cast<C*>(smraw);
@@ -730,9 +848,51 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
   // ---- load this CTA's part of the slab: asynchronous element copies
   //      straight into shared memory (no register round trip, so the strided
   //      column gathers of an alpha slab all overlap)
+  float* const smf = reinterpret_cast<float*>(smraw);
+  // amplitude (state s, string el, vector kv) of the slab
+  auto slab_get = [&](int s, size_t el, int kv) -> C {
+    if constexpr (PK) {
+      const size_t r = pk_re<NST>(s, el, KV, kv);
+      return mk<R>(smf[r], smf[r + 2]);
+    } else {
+      return sm[s * st_stride + el * KV + kv];
+    }
+  };
+  auto slab_set = [&](int s, size_t el, int kv, C v) {
+    if constexpr (PK) {
+      const size_t r = pk_re<NST>(s, el, KV, kv);
+      smf[r] = v.x;
+      smf[r + 2] = v.y;
+    } else {
+      sm[s * st_stride + el * KV + kv] = v;
+    }
+  };
   for (int s = 0; s < NST; ++s) {
     const C* gs = reinterpret_cast<const C*>(g.st[s]);
     C* ss = sm + s * st_stride;
+    if constexpr (PK) {
+      // the real and imaginary parts go to their lanes of the packed cells
+      const float* gf = reinterpret_cast<const float*>(g.st[s]);
+      if (g.dir == 1) {
+        for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
+          const int kv = idx / nel, el = idx - kv * nel;
+          const size_t r = pk_re<NST>(s, el, KV, kv);
+          const float* src = gf + 2 * ((int64_t)(v0 + kv) * g.d_b + e0 + el);
+          cp_async_4(smf + r, src);
+          cp_async_4(smf + r + 2, src + 1);
+        }
+      } else {
+        for (int idx = tid; idx < (nel << g.lgKV); idx += kThreads) {
+          const int el = idx >> g.lgKV, kv = idx & (KV - 1);
+          if (kv >= kv_eff) continue;
+          const size_t r = pk_re<NST>(s, el, KV, kv);
+          const float* src = gf + 2 * ((int64_t)(e0 + el) * g.d_b + v0 + kv);
+          cp_async_4(smf + r, src);
+          cp_async_4(smf + r + 2, src + 1);
+        }
+      }
+      continue;
+    }
     if (g.dir == 1) {
       for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
         int kv = idx / nel, el = idx - kv * nel;
@@ -861,6 +1021,32 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         drank = 0;
         dcs = 1;
       }
+      if constexpr (PK) {
+        // packed cells (vector pairs of one state, or psi and g); the work
+        // items are (orbit, packed set) pairs, chunk by chunk of 32 orbits
+        // (a class boundary never falls inside a chunk), so that short
+        // vectors with few orbits per step still fill the CTA
+        const int KC = NST == 1 ? (KV >> 1) : KV;
+        const int nk = NST == 1 ? (kv_eff + 1) >> 1 : kv_eff;
+        const int nit = (hi - lo) * nk;
+        for (int rd = 0; dealt_round<kThreads>(0, nit, rd, 0, 1); ++rd) {
+          const int it = dealt_item<kThreads>(0, nit, rd, tid, 0, 1);
+          if (it < 0) continue;
+          const int ch = it >> 5, oc = ch / nk;
+          const int o = lo + (oc << 5) + (it & 31), kc = ch - oc * nk;
+          const uint32_t desc = __ldg(olist + o);
+          switch (desc >> 24) {
+            case 1: win_orbit_pk<W, 1>(desc, F, smf, KC, kc, prog, ga, gb); break;
+            case 2: win_orbit_pk<W, 2>(desc, F, smf, KC, kc, prog, ga, gb); break;
+            case 3: win_orbit_pk<W, 3>(desc, F, smf, KC, kc, prog, ga, gb); break;
+            case 4: if constexpr (W > 4) win_orbit_pk<W, 4>(desc, F, smf, KC, kc, prog, ga, gb); break;
+            case 5: if constexpr (W > 5) win_orbit_pk<W, 5>(desc, F, smf, KC, kc, prog, ga, gb); break;
+            default: break;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       for (int rd = 0; dealt_round<kThreads>(lo, hi, rd, drank, dcs); ++rd) {
         const int o = dealt_item<kThreads>(lo, hi, rd, tid, drank, dcs);
         if (o < 0) continue;
@@ -902,7 +1088,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       }
 #pragma unroll
       for (int s = 0; s < NST; ++s) {
-        C v = cmul<R>(f, sm[s * st_stride + (size_t)el * KV + kv]);
+        C v = cmul<R>(f, slab_get(s, (size_t)el, kv));
         C* gs = reinterpret_cast<C*>(g.st[s]);
         if (g.dir == 1)
           gs[(int64_t)o * g.d_b + e] = v;
@@ -918,10 +1104,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       if (kv >= kv_eff) continue;
       C f = cmul<R>(ld_ea<R>(g.ea_other, v0 + kv), ld_ea<R>(g.ea_this, e0 + el));
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        C* q = sm + s * st_stride + (size_t)el * KV + kv;
-        *q = cmul<R>(f, *q);
-      }
+      for (int s = 0; s < 2; ++s) slab_set(s, (size_t)el, kv, cmul<R>(f, slab_get(s, (size_t)el, kv)));
     }
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     // (b) T[p][q] += sum over the slab of sign * conj(g[dst]) * psi[src] for
@@ -948,16 +1131,51 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
           drank = 0;
           dcs = 1;
         }
-        for (int rd = 0; dealt_round<kThreads>(lo, hi, rd, drank, dcs); ++rd) {
-          const int o = dealt_item<kThreads>(lo, hi, rd, tid, drank, dcs);
-          if (o < 0) continue;
+        // packed slabs: (record, vector) items, chunk by chunk of 32 records
+        // (short vectors with few records per pass still fill the CTA)
+        const int nkv = PK ? kv_eff : 1;
+        const int ilo = PK ? 0 : lo, ihi = PK ? (hi - lo) * nkv : hi;
+        for (int rd = 0; dealt_round<kThreads>(ilo, ihi, rd, drank, dcs); ++rd) {
+          const int it = dealt_item<kThreads>(ilo, ihi, rd, tid, drank, dcs);
+          if (it < 0) continue;
+          int o = it, kv0 = 0, kv1 = kv_eff;
+          if constexpr (PK) {
+            const int ch = it >> 5, oc = ch / nkv;
+            o = lo + (oc << 5) + (it & 31);
+            kv0 = ch - oc * nkv;
+            kv1 = kv0 + 1;
+          }
           TRecord rc;
           *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(rlist + o));
+          // passes that own whole slot groups (every pass of an exact
+          // covering, N = 16) skip the per-slot ownership tests
+          if constexpr (PK) {
+          if (pd.mode == 1) {
+            switch (rc.m) {
+              case 1: t_orbit<R, CS, 1, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 2: t_orbit<R, CS, 2, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 3: t_orbit<R, CS, 3, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 4: t_orbit<R, CS, 4, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              default: break;
+            }
+            continue;
+          }
+          if (pd.mode == 2) {
+            switch (rc.m) {
+              case 1: t_orbit<R, CS, 1, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 2: t_orbit<R, CS, 2, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 3: t_orbit<R, CS, 3, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              case 4: t_orbit<R, CS, 4, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+              default: break;
+            }
+            continue;
+          }
+          }
           switch (rc.m) {
-            case 1: t_orbit<R, CS, 1>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
-            case 2: t_orbit<R, CS, 2>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
-            case 3: t_orbit<R, CS, 3>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
-            case 4: t_orbit<R, CS, 4>(rc, base, st_stride, cbr, KV, kv_eff, acc, pd.keep); break;
+            case 1: t_orbit<R, CS, 1, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+            case 2: t_orbit<R, CS, 2, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+            case 3: t_orbit<R, CS, 3, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
+            case 4: t_orbit<R, CS, 4, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
             default: break;
           }
         }
@@ -1017,7 +1235,14 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
             const C* pg = base[od] + st_stride + (size_t)(dst - bd0) * KV;
             R br = 0, bi = 0;
             for (int kv = 0; kv < kv_eff; ++kv) {
-              C a = ps[kv], b = pg[kv];
+              C a, b;
+              if constexpr (PK) {
+                a = slab_get(0, (size_t)src, kv);
+                b = slab_get(1, (size_t)dst, kv);
+              } else {
+                a = ps[kv];
+                b = pg[kv];
+              }
               br = fma(b.x, a.x, fma(b.y, a.y, br));
               bi = fma(b.x, a.y, fma(-b.y, a.x, bi));
             }
@@ -1056,8 +1281,8 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       }
       const int o = v0 + kv, e = e0 + el;
       const int64_t gi = g.dir == 1 ? (int64_t)o * g.d_b + e : (int64_t)e * g.d_b + o;
-      C ps = sm[(size_t)el * KV + kv];
-      C pg = sm[st_stride + (size_t)el * KV + kv];
+      C ps = slab_get(0, (size_t)el, kv);
+      C pg = slab_get(1, (size_t)el, kv);
       if (g.W) reinterpret_cast<R*>(g.W)[gi] = pg.x * ps.y - pg.y * ps.x;
       C f = cmul<R>(ld_ea<R>(g.ea2_other, o), ld_ea<R>(g.ea2_this, e));
       if (g.has_x) {
@@ -1073,19 +1298,20 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
   }
 }
 
-template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, bool TC = false>
+template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, bool TC = false,
+          bool PK = false>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_sweep(const SweepGeom g, const __grid_constant__ typename ProgOf<R, W, (W > 0)>::type prog,
             const __grid_constant__ Mat X) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  sweep_body<R, CS, NST, VJP, W, NT, SPLIT, typename ProgOf<R, W, (W > 0)>::type, TC>(
+  sweep_body<R, CS, NST, VJP, W, NT, SPLIT, typename ProgOf<R, W, (W > 0)>::type, TC, PK>(
       g, prog, X, blockIdx.x / CS, rank, smraw);
 }
 
 // Batched sweep: one persistent launch over the slabs of many jobs (one job
 // per circuit), taken from an atomic work counter in job order.
-template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT>
+template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT, bool PK = false>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_sweep_batch(const SweepJob* jobs, int njobs, int total, int* counter) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1105,7 +1331,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const int it = s_item;
     if (it >= total) break;
     const SweepJob& J = jobs[s_job];
-    sweep_body<R, 1, NST, VJP, W, NT, SPLIT>(J.g, *reinterpret_cast<const WProg<R>*>(J.prog),
+    sweep_body<R, 1, NST, VJP, W, NT, SPLIT, WProg<R>, false, PK>(
+        J.g, *reinterpret_cast<const WProg<R>*>(J.prog),
                                              *J.X, it - J.item0, 0, smraw);
     __syncthreads();
   }
@@ -1119,10 +1346,10 @@ constexpr int window_width() {
 }
 
 template <typename R, int CS, int NST, bool VJP, int W, int NT, bool SPLIT, typename P,
-          bool TC = false>
+          bool TC = false, bool PK = false>
 void launch_sweep_t(const SweepGeom& g, const P& prog, const Mat& X,
                            int nslabs, size_t smem, cudaStream_t st) {
-  auto kern = k_sweep<R, CS, NST, VJP, W, NT, SPLIT, TC>;
+  auto kern = k_sweep<R, CS, NST, VJP, W, NT, SPLIT, TC, PK>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   static const char* names[2][2][2] = {  // [f64][reverse][beta]
@@ -1156,10 +1383,10 @@ void dispatch_cs(int CS, const SweepGeom& g, const P& prog, const Mat& X,
   }
 }
 
-template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT>
+template <typename R, int NST, bool VJP, int W, int NT, bool SPLIT, bool PK = false>
 void launch_batch_t(const SweepJob* jobs, int njobs, int total, int* counter, size_t smem,
                            int grid, cudaStream_t st) {
-  auto kern = k_sweep_batch<R, NST, VJP, W, NT, SPLIT>;
+  auto kern = k_sweep_batch<R, NST, VJP, W, NT, SPLIT, PK>;
   if (!jobs) {  // attribute only (called before a stream capture); only ever
                 // raised, since several stages share one kernel
     cudaFuncAttributes fa;
