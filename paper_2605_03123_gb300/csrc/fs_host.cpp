@@ -189,6 +189,67 @@ static inline int top3_group(uint32_t mask, int N) {
   return N >= 3 ? (int)((mask >> (N - 3)) & 7u) : 0;
 }
 
+// Order of the n items of one class (each reads and writes the 16-byte
+// slab cells A[i * ns + k], k < ns, one shared-memory instruction per k)
+// for the kernels that deal items to consecutive lanes.  A 16-byte access
+// is served eight lanes at a time, and two lanes of those eight that touch
+// different cells with equal cell index mod 8 (the same four banks) cost one
+// more wavefront.  Greedy: the items are sorted by their pattern of cell
+// offsets mod 8 (items with equal patterns and distinct first cells mod 8
+// are conflict-free together), then each aligned group of eight is grown
+// from the first remaining item by the candidate, among the next kCand,
+// that adds the fewest conflicts.  Returns the permutation (new position ->
+// old index).
+static std::vector<int> bank_order(int n, int ns, const std::vector<int>& A) {
+  constexpr int kCand = 128;
+  std::vector<int> rem(n);
+  std::vector<uint64_t> sig(n);
+  for (int i = 0; i < n; ++i) {
+    rem[i] = i;
+    uint64_t s = 0;
+    for (int k = 1; k < ns && k < 22; ++k)
+      s |= (uint64_t)((A[(size_t)i * ns + k] - A[(size_t)i * ns]) & 7) << (3 * (k - 1));
+    sig[i] = s;
+  }
+  std::stable_sort(rem.begin(), rem.end(), [&](int u, int v) {
+    if (sig[u] != sig[v]) return sig[u] < sig[v];
+    return A[(size_t)u * ns] < A[(size_t)v * ns];
+  });
+  std::vector<int> out;
+  out.reserve(n);
+  std::vector<int> grp;
+  while (!rem.empty()) {
+    grp.assign(1, rem.front());
+    rem.erase(rem.begin());
+    while (grp.size() < 8 && !rem.empty()) {
+      int best = 0, bc = 1 << 30;
+      const int nc = std::min<int>(kCand, (int)rem.size());
+      for (int j = 0; j < nc && bc > 0; ++j) {
+        const int i = rem[j];
+        int c = 0;
+        for (int k = 0; k < ns; ++k) {
+          const int cell = A[(size_t)i * ns + k];
+          for (int g : grp) {
+            const int o = A[(size_t)g * ns + k];
+            if (o != cell && ((o ^ cell) & 7) == 0) {
+              ++c;
+              break;
+            }
+          }
+        }
+        if (c < bc) {
+          bc = c;
+          best = j;
+        }
+      }
+      grp.push_back(rem[best]);
+      rem.erase(rem.begin() + best);
+    }
+    out.insert(out.end(), grp.begin(), grp.end());
+  }
+  return out;
+}
+
 // For the window [a, a+W): every outside configuration O with
 // m = n - |O| in 1 .. W-1 is one orbit.  With c_lo = |O below a|, the address
 // of O u S (S inside the window) is R_O + F[a][c_lo][S], where R_O sums
@@ -256,16 +317,6 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
       const uint64_t pu = C(W - 2, u - 1), pv = C(W - 2, v - 1);
       return pu != pv ? pu > pv : C(W, u) > C(W, v);
     });
-    for (int m : order) {
-      if (cls[m].empty()) continue;
-      orbits.insert(orbits.end(), cls[m].begin(), cls[m].end());
-      okey.insert(okey.end(), ckey[m].begin(), ckey[m].end());
-      while ((orbits.size() - off[a]) % 32) {
-        orbits.push_back(0u);
-        okey.push_back(0);
-      }
-    }
-
     for (int clo = 0; clo <= n; ++clo)
       for (int S = 0; S < (1 << W); ++S) {
         uint64_t f = 0;
@@ -274,6 +325,28 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
           if ((S >> b) & 1) f += C(a + b, clo + (j++) + 1);
         offs[(((size_t)a * (n + 1) + clo) << W) + S] = (uint16_t)std::min<uint64_t>(f, 65535);
       }
+    for (int m : order) {
+      if (cls[m].empty()) continue;
+      // lanes of one shared-memory phase on distinct bank groups
+      const int no_m = (int)cls[m].size(), ns = (int)C(W, m);
+      std::vector<int> A((size_t)no_m * ns);
+      for (int i = 0; i < no_m; ++i) {
+        const uint32_t desc = cls[m][i];
+        const int RO = desc & 0xFFFF, clo = (desc >> 16) & 0xFF;
+        int k = 0;
+        for (int S = 0; S < (1 << W); ++S)
+          if (__builtin_popcount(S) == m)
+            A[(size_t)i * ns + k++] = RO + offs[(((size_t)a * (n + 1) + clo) << W) + S];
+      }
+      for (int i : bank_order(no_m, ns, A)) {
+        orbits.push_back(cls[m][i]);
+        okey.push_back(ckey[m][i]);
+      }
+      while ((orbits.size() - off[a]) % 32) {
+        orbits.push_back(0u);
+        okey.push_back(0);
+      }
+    }
   }
   off[npos] = (int)orbits.size();
 }
@@ -446,8 +519,15 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
     // records (m = 0, skipped by the kernels) to a multiple of 32.
     for (int m : {2, 3, 1, 4}) {
       if (rcls[m].empty()) continue;
-      recs.insert(recs.end(), rcls[m].begin(), rcls[m].end());
-      rkey.insert(rkey.end(), rck[m].begin(), rck[m].end());
+      // lanes of one shared-memory phase on distinct bank groups
+      const int nr = (int)rcls[m].size(), ns = (int)C(4, m);
+      std::vector<int> A((size_t)nr * ns);
+      for (int i = 0; i < nr; ++i)
+        for (int k = 0; k < ns; ++k) A[(size_t)i * ns + k] = rcls[m][i].addr[k];
+      for (int i : bank_order(nr, ns, A)) {
+        recs.push_back(rcls[m][i]);
+        rkey.push_back(rck[m][i]);
+      }
       while ((recs.size() - ps.rec0) % 32) {
         recs.push_back(TRecord{});
         rkey.push_back(0);
