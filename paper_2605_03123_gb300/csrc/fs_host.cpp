@@ -506,6 +506,15 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
           g |= (uint8_t)(acc << (j + 1));  // bit j+1: parity of O before q_{j+1}
         }
         r.gbits = g;
+        // omega(S) for each local subset S in the record's order
+        r.flips = 0;
+        for (int s = 0, kk = 0; s < 16; ++s) {
+          if (__builtin_popcount(s) != m) continue;
+          int f = 0;
+          for (int j = 1; j < 4; ++j)
+            if ((s >> j) & 1) f ^= (g >> j) & 1;
+          r.flips |= (uint16_t)(f << kk++);
+        }
         rcls[m].push_back(r);
         rck[m].push_back((uint8_t)top3_group(omask, N));
         if (ne == 0) break;

@@ -113,7 +113,7 @@ struct alignas(16) TRecord {
   uint16_t addr[6];  // addresses of O u S, S in ascending local-mask order
   uint8_t m;         // electrons inside the subset
   uint8_t gbits;     // bit j: parity of |O| between q_0 and q_j (j = 1..3)
-  uint16_t pad;
+  uint16_t flips;    // bit k: omega(S_k), the parity of the gbits of S_k's orbitals
 };
 // rkey[i]: occupation of the top three orbitals in record i's configuration
 // outside the subset (a 3-bit number).
@@ -315,17 +315,31 @@ void launch_string_phase(const Space* sp, void* out, int dtype, const StrPhase& 
 // orbitals inside the window [a[s], a[s] + W); u = p - a[s] is the local
 // index of the rotated pair (p, p+1); pat[s] >= 0 names the step's
 // u-sequence among the compile-time window patterns (-1: none).
-// Coefficients c, Re s, Im s of each rotation: complex128 keeps them as
-// doubles; complex64 keeps each as a pair (x, x) (and -Re s, -Im s as
-// pairs) for the packed two-lane FP32 updates, read as floats elsewhere.
+// Coefficients of each rotation G = [[c, s], [-s*, c]] (c >= 0, as the
+// adjacent decomposition makes it).  complex128 keeps c, Re s, Im s as
+// doubles and updates a pair directly: x' = c x + s y, y' = -s* x + c y.
+// complex64 keeps the shear form G = [[1, tau], [0, 1]] [[1, 0], [sig, 1]]
+// [[1, tau], [0, 1]] with tau = s / (1 + c) and sig = -s* (so 1 + tau sig
+// = c and tau (1 + c) = s): x += tau y; y += sig x; x += tau y, three
+// complex multiply-adds that each update one amplitude in place, so a
+// rotation leaves its amplitudes in the registers it found them in.  Since
+// c >= 0, |tau| <= |s| <= 1.  Each complex64 coefficient is stored as a pair
+// (x, x) for the packed two-lane FP32 updates (and Im tau once more negated),
+// read as floats by the one-lane updates.
+template <typename R>
+struct GCoef {  // one rotation, direct form
+  R c, sr, si;
+};
+template <>
+struct GCoef<float> {  // one rotation, shear form
+  float tr, ti, gr, gi;
+};
 template <typename R>
 struct WCoef {
   R c[kMaxGivens];
   R sr[kMaxGivens];
   R si[kMaxGivens];
-  __host__ __device__ R cf(int q) const { return c[q]; }
-  __host__ __device__ R srf(int q) const { return sr[q]; }
-  __host__ __device__ R sif(int q) const { return si[q]; }
+  __host__ __device__ GCoef<R> coef(int q) const { return GCoef<R>{c[q], sr[q], si[q]}; }
   __host__ void set(int q, double cv, double srv, double siv) {
     c[q] = (R)cv;
     sr[q] = (R)srv;
@@ -334,21 +348,21 @@ struct WCoef {
 };
 template <>
 struct WCoef<float> {
-  float2 c2[kMaxGivens];
-  float2 sr2[kMaxGivens];
-  float2 si2[kMaxGivens];
-  float2 nsr2[kMaxGivens];
-  float2 nsi2[kMaxGivens];
-  __host__ __device__ float cf(int q) const { return c2[q].x; }
-  __host__ __device__ float srf(int q) const { return sr2[q].x; }
-  __host__ __device__ float sif(int q) const { return si2[q].x; }
+  float2 tr2[kMaxGivens];   // Re tau
+  float2 ti2[kMaxGivens];   // Im tau
+  float2 nti2[kMaxGivens];  // -Im tau
+  float2 gr2[kMaxGivens];   // Re sig = -Re s
+  float2 gi2[kMaxGivens];   // Im sig = Im s
+  __host__ __device__ GCoef<float> coef(int q) const {
+    return GCoef<float>{tr2[q].x, ti2[q].x, gr2[q].x, gi2[q].x};
+  }
   __host__ void set(int q, double cv, double srv, double siv) {
-    const float c = (float)cv, sr = (float)srv, si = (float)siv;
-    c2[q] = make_float2(c, c);
-    sr2[q] = make_float2(sr, sr);
-    si2[q] = make_float2(si, si);
-    nsr2[q] = make_float2(-sr, -sr);
-    nsi2[q] = make_float2(-si, -si);
+    const float tr = (float)(srv / (1.0 + cv)), ti = (float)(siv / (1.0 + cv));
+    tr2[q] = make_float2(tr, tr);
+    ti2[q] = make_float2(ti, ti);
+    nti2[q] = make_float2(-ti, -ti);
+    gr2[q] = make_float2((float)-srv, (float)-srv);
+    gi2[q] = make_float2((float)siv, (float)siv);
   }
 };
 template <typename R>

@@ -72,24 +72,39 @@ __host__ __device__ constexpr int win_npairs(int W, int M, int u) {
   return n;
 }
 
+// One Givens update of the pair (x, y) in the form its coefficients are
+// kept in: complex128 directly, complex64 as three in-place shears
+// (x += tau y; y += sig x; x += tau y), each a complex multiply-add of two
+// fused multiply-adds per part.
+__device__ __forceinline__ void givens_upd(cx_t<double>& x, cx_t<double>& y, GCoef<double> k) {
+  givens2<double>(x, y, k.c, k.sr, k.si);
+}
+__device__ __forceinline__ void givens_upd(cx_t<float>& x, cx_t<float>& y, GCoef<float> k) {
+  x.x = fmaf(-k.ti, y.y, fmaf(k.tr, y.x, x.x));
+  x.y = fmaf(k.ti, y.x, fmaf(k.tr, y.y, x.y));
+  y.x = fmaf(-k.gi, x.y, fmaf(k.gr, x.x, y.x));
+  y.y = fmaf(k.gi, x.x, fmaf(k.gr, x.y, y.y));
+  x.x = fmaf(-k.ti, y.y, fmaf(k.tr, y.x, x.x));
+  x.y = fmaf(k.ti, y.x, fmaf(k.tr, y.y, x.y));
+}
+
 template <int W, int M, int U, int J, typename R, int NV, int NS>
-__device__ __forceinline__ void win_pair(cx_t<R> (&v)[NV][NS], R c, R sr, R si) {
+__device__ __forceinline__ void win_pair(cx_t<R> (&v)[NV][NS], GCoef<R> k) {
   constexpr int sm = win_src_mask(W, M, U, J);
   constexpr int a = win_index(W, M, sm);
   constexpr int b = win_index(W, M, sm ^ (1 << U) ^ (1 << (U + 1)));
 #pragma unroll
-  for (int x = 0; x < NV; ++x) givens2<R>(v[x][a], v[x][b], c, sr, si);
+  for (int x = 0; x < NV; ++x) givens_upd(v[x][a], v[x][b], k);
 }
 template <int W, int M, int U, typename R, int NV, int NS, int... J>
-__device__ __forceinline__ void win_pairs_seq(cx_t<R> (&v)[NV][NS], R c, R sr, R si,
+__device__ __forceinline__ void win_pairs_seq(cx_t<R> (&v)[NV][NS], GCoef<R> k,
                                               std::integer_sequence<int, J...>) {
-  (win_pair<W, M, U, J, R, NV, NS>(v, c, sr, si), ...);
+  (win_pair<W, M, U, J, R, NV, NS>(v, k), ...);
 }
 template <int W, int M, int U, typename R, int NV, int NS>
-__device__ __forceinline__ void win_pairs(cx_t<R> (&v)[NV][NS], R c, R sr, R si) {
+__device__ __forceinline__ void win_pairs(cx_t<R> (&v)[NV][NS], GCoef<R> k) {
   if constexpr (U + 1 < W)
-    win_pairs_seq<W, M, U, R, NV, NS>(v, c, sr, si,
-                                      std::make_integer_sequence<int, win_npairs(W, M, U)>{});
+    win_pairs_seq<W, M, U, R, NV, NS>(v, k, std::make_integer_sequence<int, win_npairs(W, M, U)>{});
 }
 
 // Window patterns.  The greedy window schedule of the adjacent
@@ -126,7 +141,7 @@ constexpr int win_npat() {
 template <int W, int M, typename R, int NV, int NS, int... U, int... K>
 __device__ __forceinline__ void win_seq(cx_t<R> (&v)[NV][NS], const WProg<R>& prog, int ga,
                                         useq<U...>, std::integer_sequence<int, K...>) {
-  (win_pairs<W, M, U, R, NV, NS>(v, prog.cf(ga + K), prog.srf(ga + K), prog.sif(ga + K)), ...);
+  (win_pairs<W, M, U, R, NV, NS>(v, prog.coef(ga + K)), ...);
 }
 template <int W, int M, typename R, int NV, int NS, int I>
 __device__ __forceinline__ bool win_pattern(int pid, cx_t<R> (&v)[NV][NS], const WProg<R>& prog,
@@ -430,15 +445,15 @@ __device__ __forceinline__ void win_apply(cx_t<R> (&v)[NV][NS], const WProg<R>& 
   if (win_patterns<W, M, R, NV, NS>(pid, v, prog, ga, std::make_index_sequence<(size_t)npat>{}))
     return;
   for (int q = ga; q < gb; ++q) {
-    const R c = prog.cf(q), sr = prog.srf(q), si = prog.sif(q);
+    const GCoef<R> k = prog.coef(q);
     switch (prog.u[q]) {
-      case 0: win_pairs<W, M, 0, R, NV, NS>(v, c, sr, si); break;
-      case 1: win_pairs<W, M, 1, R, NV, NS>(v, c, sr, si); break;
-      case 2: win_pairs<W, M, 2, R, NV, NS>(v, c, sr, si); break;
-      case 3: win_pairs<W, M, 3, R, NV, NS>(v, c, sr, si); break;
-      case 4: win_pairs<W, M, 4, R, NV, NS>(v, c, sr, si); break;
-      case 5: win_pairs<W, M, 5, R, NV, NS>(v, c, sr, si); break;
-      case 6: win_pairs<W, M, 6, R, NV, NS>(v, c, sr, si); break;
+      case 0: win_pairs<W, M, 0, R, NV, NS>(v, k); break;
+      case 1: win_pairs<W, M, 1, R, NV, NS>(v, k); break;
+      case 2: win_pairs<W, M, 2, R, NV, NS>(v, k); break;
+      case 3: win_pairs<W, M, 3, R, NV, NS>(v, k); break;
+      case 4: win_pairs<W, M, 4, R, NV, NS>(v, k); break;
+      case 5: win_pairs<W, M, 5, R, NV, NS>(v, k); break;
+      case 6: win_pairs<W, M, 6, R, NV, NS>(v, k); break;
       default: break;
     }
   }
@@ -503,34 +518,36 @@ __device__ __forceinline__ void win_orbit(uint32_t desc, const uint16_t* F, cx_t
 // 4c, lane 1 at 4c + 1, imaginary parts 2 further.
 //
 // Packed Givens update of the pairs (x, y) of both lanes, the same
-// operations as givens2 lane by lane (so the results are bit-identical):
-//   x' = c x + s y,   y' = -s* x + c y.
+// operations as the one-lane shear update lane by lane (so the results are
+// bit-identical): x += tau y; y += sig x; x += tau y, every amplitude
+// updated in place.
 __device__ __forceinline__ void givens2_pk(float2& xr, float2& xi, float2& yr, float2& yi,
-                                           float2 c, float2 sr, float2 si, float2 nsr,
-                                           float2 nsi) {
-  const float2 xr2 = __ffma2_rn(c, xr, __ffma2_rn(sr, yr, __fmul2_rn(nsi, yi)));
-  const float2 xi2 = __ffma2_rn(c, xi, __ffma2_rn(sr, yi, __fmul2_rn(si, yr)));
-  const float2 yr2 = __ffma2_rn(c, yr, __ffma2_rn(nsr, xr, __fmul2_rn(nsi, xi)));
-  const float2 yi2 = __ffma2_rn(c, yi, __ffma2_rn(si, xr, __fmul2_rn(nsr, xi)));
-  xr = xr2;
-  xi = xi2;
-  yr = yr2;
-  yi = yi2;
+                                           float2 tr, float2 ti, float2 nti, float2 gr,
+                                           float2 gi, float2 ngi) {
+  xr = __ffma2_rn(nti, yi, __ffma2_rn(tr, yr, xr));
+  xi = __ffma2_rn(ti, yr, __ffma2_rn(tr, yi, xi));
+  yr = __ffma2_rn(ngi, xi, __ffma2_rn(gr, xr, yr));
+  yi = __ffma2_rn(gi, xr, __ffma2_rn(gr, xi, yi));
+  xr = __ffma2_rn(nti, yi, __ffma2_rn(tr, yr, xr));
+  xi = __ffma2_rn(ti, yr, __ffma2_rn(tr, yi, xi));
 }
 template <int W, int M, int U, int J, int NS>
-__device__ __forceinline__ void win_pair_pk(float2 (&vr)[NS], float2 (&vi)[NS], const WProg<float>& prog,
-                                            int q) {
+__device__ __forceinline__ void win_pair_pk(float2 (&vr)[NS], float2 (&vi)[NS], float2 tr,
+                                            float2 ti, float2 nti, float2 gr, float2 gi,
+                                            float2 ngi) {
   constexpr int sm = win_src_mask(W, M, U, J);
   constexpr int a = win_index(W, M, sm);
   constexpr int b = win_index(W, M, sm ^ (1 << U) ^ (1 << (U + 1)));
-  givens2_pk(vr[a], vi[a], vr[b], vi[b], prog.c2[q], prog.sr2[q], prog.si2[q], prog.nsr2[q],
-             prog.nsi2[q]);
+  givens2_pk(vr[a], vi[a], vr[b], vi[b], tr, ti, nti, gr, gi, ngi);
 }
 template <int W, int M, int U, int NS, int... J>
 __device__ __forceinline__ void win_pairs_pk_seq(float2 (&vr)[NS], float2 (&vi)[NS],
                                                  const WProg<float>& prog, int q,
                                                  std::integer_sequence<int, J...>) {
-  (win_pair_pk<W, M, U, J, NS>(vr, vi, prog, q), ...);
+  const float2 tr = prog.tr2[q], ti = prog.ti2[q], nti = prog.nti2[q], gr = prog.gr2[q],
+               gi = prog.gi2[q];
+  const float2 ngi = __fmul2_rn(gi, make_float2(-1.f, -1.f));
+  (win_pair_pk<W, M, U, J, NS>(vr, vi, tr, ti, nti, gr, gi, ngi), ...);
 }
 template <int W, int M, int U, int NS>
 __device__ __forceinline__ void win_pairs_pk(float2 (&vr)[NS], float2 (&vi)[NS],
@@ -584,6 +601,25 @@ __device__ __forceinline__ size_t pk_re(int s, size_t el, int KV, int kv) {
   else
     return 4 * (el * (size_t)KV + (size_t)kv) + (size_t)s;
 }
+// Quotient and remainder of idx by n along idx = i0, i0 + step, ...: one
+// division when the walk starts, then an add and a compare per step.
+struct DivWalk {
+  int n, q, r, a, b;  // a = idx / n, b = idx % n
+  __device__ __forceinline__ DivWalk(int i0, int step, int n_) : n(n_) {
+    a = i0 / n;
+    b = i0 - a * n;
+    q = step / n;
+    r = step - q * n;
+  }
+  __device__ __forceinline__ void next() {
+    a += q;
+    b += r;
+    if (b >= n) {
+      b -= n;
+      ++a;
+    }
+  }
+};
 __device__ __forceinline__ void cp_async_4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
@@ -634,20 +670,6 @@ __device__ __forceinline__ void t_terms(const cx_t<R> (&ps)[NS], const cx_t<R> (
                                         std::integer_sequence<int, J...>) {
   (t_term<R, M, J, NS, DIAG, KEEP>(ps, pg, acc, keep), ...);
 }
-template <int M, int K>
-__device__ __forceinline__ int t_flip(int gb) {
-  constexpr int S = win_mask(4, M, K);
-  int f = 0;
-#pragma unroll
-  for (int j = 1; j < 4; ++j)
-    if ((S >> j) & 1) f ^= (gb >> j) & 1;
-  return f;
-}
-template <int M, int... K>
-__device__ __forceinline__ void t_flips(int gb, int (&fl)[sizeof...(K)],
-                                        std::integer_sequence<int, K...>) {
-  ((fl[K] = t_flip<M, K>(gb)), ...);
-}
 template <typename R, int CS, int M, bool PK, bool DIAG = true, bool KEEP = true>
 __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base, size_t st_stride,
                                         const int (&cbr)[CS + 1], int KV, int kv0, int kv1,
@@ -672,30 +694,70 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
       ad[k] = e * KV;
     }
   }
-  int fl[NS];
-  t_flips<M>(rc.gbits, fl, std::make_integer_sequence<int, NS>{});
+  const uint32_t fls = rc.flips;
   for (int kv = kv0; kv < kv1; ++kv) {
     C ps[NS], pg[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if constexpr (PK) {
-        // packed cell (Re psi, Re g, Im psi, Im g)
+        // packed cell (Re psi, Re g, Im psi, Im g), signs flipped by omega
         const float4 t = reinterpret_cast<const float4*>(base[0])[ad[k] + kv];
-        ps[k] = mk<R>(t.x, t.z);
-        pg[k] = mk<R>(t.y, t.w);
+        const uint32_t sg = ((fls >> k) & 1u) << 31;
+        ps[k] = mk<R>(__uint_as_float(__float_as_uint(t.x) ^ sg),
+                      __uint_as_float(__float_as_uint(t.z) ^ sg));
+        pg[k] = mk<R>(__uint_as_float(__float_as_uint(t.y) ^ sg),
+                      __uint_as_float(__float_as_uint(t.w) ^ sg));
       } else {
         C* b0 = base[CS > 1 ? own[k] : 0];
         ps[k] = b0[ad[k] + kv];
         pg[k] = b0[st_stride + ad[k] + kv];
-      }
-      if (fl[k]) {
-        ps[k].x = -ps[k].x;
-        ps[k].y = -ps[k].y;
-        pg[k].x = -pg[k].x;
-        pg[k].y = -pg[k].y;
+        if ((fls >> k) & 1u) {
+          ps[k].x = -ps[k].x;
+          ps[k].y = -ps[k].y;
+          pg[k].x = -pg[k].x;
+          pg[k].y = -pg[k].y;
+        }
       }
     }
     t_terms<R, M, NS, DIAG, KEEP>(ps, pg, acc, keep, std::make_integer_sequence<int, 6 * 16>{});
+  }
+}
+
+// One record of a transition pass, by its class and the pass's mode (1:
+// the pass owns exactly its twelve off-diagonal slots; 2: all sixteen; 0:
+// ownership tested per slot).
+template <typename R, int CS, bool PK>
+__device__ __forceinline__ void t_record(int mode, const TRecord& rc, cx_t<R>* const* base,
+                                         size_t st_stride, const int (&cbr)[CS + 1], int KV,
+                                         int kv0, int kv1, R (&acc)[32], uint32_t keep) {
+  if constexpr (PK) {
+    if (mode == 1) {
+      switch (rc.m) {
+        case 1: t_orbit<R, CS, 1, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 2: t_orbit<R, CS, 2, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 3: t_orbit<R, CS, 3, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 4: t_orbit<R, CS, 4, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        default: break;
+      }
+      return;
+    }
+    if (mode == 2) {
+      switch (rc.m) {
+        case 1: t_orbit<R, CS, 1, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 2: t_orbit<R, CS, 2, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 3: t_orbit<R, CS, 3, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        case 4: t_orbit<R, CS, 4, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+        default: break;
+      }
+      return;
+    }
+  }
+  switch (rc.m) {
+    case 1: t_orbit<R, CS, 1, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 2: t_orbit<R, CS, 2, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 3: t_orbit<R, CS, 3, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 4: t_orbit<R, CS, 4, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    default: break;
   }
 }
 
@@ -874,8 +936,9 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       // the real and imaginary parts go to their lanes of the packed cells
       const float* gf = reinterpret_cast<const float*>(g.st[s]);
       if (g.dir == 1) {
-        for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
-          const int kv = idx / nel, el = idx - kv * nel;
+        DivWalk dw(tid, kThreads, nel > 0 ? nel : 1);
+        for (int idx = tid; idx < kv_eff * nel; idx += kThreads, dw.next()) {
+          const int kv = dw.a, el = dw.b;
           const size_t r = pk_re<NST>(s, el, KV, kv);
           const float* src = gf + 2 * ((int64_t)(v0 + kv) * g.d_b + e0 + el);
           cp_async_4(smf + r, src);
@@ -894,8 +957,9 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       continue;
     }
     if (g.dir == 1) {
-      for (int idx = tid; idx < kv_eff * nel; idx += kThreads) {
-        int kv = idx / nel, el = idx - kv * nel;
+      DivWalk dw(tid, kThreads, nel > 0 ? nel : 1);
+      for (int idx = tid; idx < kv_eff * nel; idx += kThreads, dw.next()) {
+        const int kv = dw.a, el = dw.b;
         cp_async_elem(ss + (size_t)el * KV + kv, gs + (int64_t)(v0 + kv) * g.d_b + e0 + el);
       }
     } else {
@@ -1032,7 +1096,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         for (int rd = 0; dealt_round<kThreads>(0, nit, rd, 0, 1); ++rd) {
           const int it = dealt_item<kThreads>(0, nit, rd, tid, 0, 1);
           if (it < 0) continue;
-          const int ch = it >> 5, oc = ch / nk;
+          const int ch = it >> 5, oc = nk == 1 ? ch : ch / nk;
           const int o = lo + (oc << 5) + (it & 31), kc = ch - oc * nk;
           const uint32_t desc = __ldg(olist + o);
           switch (desc >> 24) {
@@ -1069,11 +1133,12 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
     // ---- epilogue: phases, store
     if (g.has_x) build_cross_tables<R>(g, X, v0, kv_eff, w, tab, tid, kThreads);
     const int tot = g.dir == 1 ? kv_eff * nel : (nel << g.lgKV);
-    for (int idx = tid; idx < tot; idx += kThreads) {
+    DivWalk dw(tid, kThreads, nel > 0 ? nel : 1);
+    for (int idx = tid; idx < tot; idx += kThreads, dw.next()) {
       int kv, el;
       if (g.dir == 1) {
-        kv = idx / nel;
-        el = idx - kv * nel;
+        kv = dw.a;
+        el = dw.b;
       } else {
         el = idx >> g.lgKV;
         kv = idx & (KV - 1);
@@ -1116,6 +1181,32 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
       for (int i = tid; i < g.npass * 32; i += kThreads) tsm[i] = 0;
       __syncthreads();
       const int lane = tid & 31;
+      if constexpr (CS == 1 && PK) {
+        // one CTA: each warp takes whole units (pass ip, chunks c = qq mod 4
+        // of its (record, vector) items, 32 records a chunk, interleaved so
+        // that the units of a pass carry the same mix of classes) and
+        // reduces once per unit; units are dealt round-robin over the
+        // warps in pass order, so the passes that also own diagonals (the
+        // first ones of the covering) fall on different warps
+        const int warp = tid >> 5, nkv = kv_eff;
+        for (int u = warp; u < g.npass * 4; u += kThreads / 32) {
+          const int ip = u >> 2, qq = u & 3;
+          const TPassDev pd = g.tpass[ip];
+          R acc[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = 0;
+          const int nch = ((pd.rec1 - pd.rec0) >> 5) * nkv;
+          for (int ch = qq; ch < nch; ch += 4) {
+            const int oc = nkv == 1 ? ch : ch / nkv;
+            const int o = pd.rec0 + (oc << 5) + lane, kv0 = ch - oc * nkv;
+            TRecord rc;
+            *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
+            t_record<R, CS, PK>(pd.mode, rc, base, st_stride, cbr, KV, kv0, kv0 + 1, acc, pd.keep);
+          }
+          const R v = warp_transpose_sum<R>(acc, lane);
+          if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + ip * 32 + lane, v);
+        }
+      } else {
       for (int ip = 0; ip < g.npass; ++ip) {
         const TPassDev pd = g.tpass[ip];
         R acc[32];
@@ -1140,7 +1231,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
           if (it < 0) continue;
           int o = it, kv0 = 0, kv1 = kv_eff;
           if constexpr (PK) {
-            const int ch = it >> 5, oc = ch / nkv;
+            const int ch = it >> 5, oc = nkv == 1 ? ch : ch / nkv;
             o = lo + (oc << 5) + (it & 31);
             kv0 = ch - oc * nkv;
             kv1 = kv0 + 1;
@@ -1181,6 +1272,7 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         }
         const R v = warp_transpose_sum<R>(acc, lane);
         if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + ip * 32 + lane, v);
+      }
       }
       __syncthreads();
       for (int i = tid; i < g.npass * 32; i += kThreads) {
@@ -1269,11 +1361,12 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
     //     follows), then the second phase, then store both states
     if (g.has_x) build_cross_tables<R>(g, X, v0, kv_eff, w, tab, tid, kThreads);
     const int tot = g.dir == 1 ? kv_eff * nel : (nel << g.lgKV);
-    for (int idx = tid; idx < tot; idx += kThreads) {
+    DivWalk dw(tid, kThreads, nel > 0 ? nel : 1);
+    for (int idx = tid; idx < tot; idx += kThreads, dw.next()) {
       int kv, el;
       if (g.dir == 1) {
-        kv = idx / nel;
-        el = idx - kv * nel;
+        kv = dw.a;
+        el = dw.b;
       } else {
         el = idx >> g.lgKV;
         kv = idx & (KV - 1);
