@@ -723,40 +723,30 @@ __device__ __forceinline__ void t_orbit(const TRecord& rc, cx_t<R>* const* base,
   }
 }
 
-// One record of a transition pass, by its class and the pass's mode (1:
-// the pass owns exactly its twelve off-diagonal slots; 2: all sixteen; 0:
-// ownership tested per slot).
+// One record of a transition pass, by its class and whether the pass
+// evaluates diagonal slots.  Every evaluated slot is accumulated; slots the
+// pass does not own (pairs an inexact covering repeats, diagonals owned
+// elsewhere) are dropped when the pass's sums are reduced, which costs a few
+// repeated multiply-adds instead of a test per slot and string.
 template <typename R, int CS, bool PK>
-__device__ __forceinline__ void t_record(int mode, const TRecord& rc, cx_t<R>* const* base,
+__device__ __forceinline__ void t_record(bool diag, const TRecord& rc, cx_t<R>* const* base,
                                          size_t st_stride, const int (&cbr)[CS + 1], int KV,
                                          int kv0, int kv1, R (&acc)[32], uint32_t keep) {
-  if constexpr (PK) {
-    if (mode == 1) {
-      switch (rc.m) {
-        case 1: t_orbit<R, CS, 1, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 2: t_orbit<R, CS, 2, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 3: t_orbit<R, CS, 3, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 4: t_orbit<R, CS, 4, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        default: break;
-      }
-      return;
+  if (!diag) {
+    switch (rc.m) {
+      case 1: t_orbit<R, CS, 1, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+      case 2: t_orbit<R, CS, 2, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+      case 3: t_orbit<R, CS, 3, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+      case 4: t_orbit<R, CS, 4, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+      default: break;
     }
-    if (mode == 2) {
-      switch (rc.m) {
-        case 1: t_orbit<R, CS, 1, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 2: t_orbit<R, CS, 2, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 3: t_orbit<R, CS, 3, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        case 4: t_orbit<R, CS, 4, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-        default: break;
-      }
-      return;
-    }
+    return;
   }
   switch (rc.m) {
-    case 1: t_orbit<R, CS, 1, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-    case 2: t_orbit<R, CS, 2, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-    case 3: t_orbit<R, CS, 3, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
-    case 4: t_orbit<R, CS, 4, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 1: t_orbit<R, CS, 1, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 2: t_orbit<R, CS, 2, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 3: t_orbit<R, CS, 3, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
+    case 4: t_orbit<R, CS, 4, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, keep); break;
     default: break;
   }
 }
@@ -1093,12 +1083,23 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
         const int KC = NST == 1 ? (KV >> 1) : KV;
         const int nk = NST == 1 ? (kv_eff + 1) >> 1 : kv_eff;
         const int nit = (hi - lo) * nk;
+        // the descriptor of the next round is loaded while this one runs
+        auto item_orbit = [&](int it) {
+          const int ch = it >> 5, oc = nk == 1 ? ch : ch / nk;
+          return lo + (oc << 5) + (it & 31);
+        };
+        int it_next = dealt_round<kThreads>(0, nit, 0, 0, 1) ? dealt_item<kThreads>(0, nit, 0, tid, 0, 1) : -1;
+        uint32_t desc_next = it_next >= 0 ? __ldg(olist + item_orbit(it_next)) : 0u;
         for (int rd = 0; dealt_round<kThreads>(0, nit, rd, 0, 1); ++rd) {
-          const int it = dealt_item<kThreads>(0, nit, rd, tid, 0, 1);
+          const int it = it_next;
+          const uint32_t desc = desc_next;
+          it_next = dealt_round<kThreads>(0, nit, rd + 1, 0, 1)
+                        ? dealt_item<kThreads>(0, nit, rd + 1, tid, 0, 1)
+                        : -1;
+          if (it_next >= 0) desc_next = __ldg(olist + item_orbit(it_next));
           if (it < 0) continue;
           const int ch = it >> 5, oc = nk == 1 ? ch : ch / nk;
-          const int o = lo + (oc << 5) + (it & 31), kc = ch - oc * nk;
-          const uint32_t desc = __ldg(olist + o);
+          const int kc = ch - oc * nk;
           switch (desc >> 24) {
             case 1: win_orbit_pk<W, 1>(desc, F, smf, KC, kc, prog, ga, gb); break;
             case 2: win_orbit_pk<W, 2>(desc, F, smf, KC, kc, prog, ga, gb); break;
@@ -1196,12 +1197,21 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
 #pragma unroll
           for (int i = 0; i < 32; ++i) acc[i] = 0;
           const int nch = ((pd.rec1 - pd.rec0) >> 5) * nkv;
+          // chunk ch = (record chunk oc, vector kv0), walked without a
+          // division per chunk; the record of the next chunk is loaded
+          // while this one runs
+          auto rec_of = [&](int oc) {
+            return __ldg(reinterpret_cast<const uint4*>(g.trec + pd.rec0 + (oc << 5) + lane));
+          };
+          DivWalk cw(qq, 4, nkv);
+          uint4 rnext = qq < nch ? rec_of(cw.a) : make_uint4(0, 0, 0, 0);
           for (int ch = qq; ch < nch; ch += 4) {
-            const int oc = nkv == 1 ? ch : ch / nkv;
-            const int o = pd.rec0 + (oc << 5) + lane, kv0 = ch - oc * nkv;
+            const int kv0 = cw.b;
+            cw.next();
             TRecord rc;
-            *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(g.trec + o));
-            t_record<R, CS, PK>(pd.mode, rc, base, st_stride, cbr, KV, kv0, kv0 + 1, acc, pd.keep);
+            *reinterpret_cast<uint4*>(&rc) = rnext;
+            if (ch + 4 < nch) rnext = rec_of(cw.a);
+            t_record<R, CS, PK>((pd.keep & 0x8421u) != 0, rc, base, st_stride, cbr, KV, kv0, kv0 + 1, acc, pd.keep);
           }
           const R v = warp_transpose_sum<R>(acc, lane);
           if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + ip * 32 + lane, v);
@@ -1238,37 +1248,8 @@ __device__ __forceinline__ void sweep_body(const SweepGeom& g, const P& prog, co
           }
           TRecord rc;
           *reinterpret_cast<uint4*>(&rc) = __ldg(reinterpret_cast<const uint4*>(rlist + o));
-          // passes that own whole slot groups (every pass of an exact
-          // covering, N = 16) skip the per-slot ownership tests
-          if constexpr (PK) {
-          if (pd.mode == 1) {
-            switch (rc.m) {
-              case 1: t_orbit<R, CS, 1, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 2: t_orbit<R, CS, 2, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 3: t_orbit<R, CS, 3, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 4: t_orbit<R, CS, 4, PK, false, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              default: break;
-            }
-            continue;
-          }
-          if (pd.mode == 2) {
-            switch (rc.m) {
-              case 1: t_orbit<R, CS, 1, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 2: t_orbit<R, CS, 2, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 3: t_orbit<R, CS, 3, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              case 4: t_orbit<R, CS, 4, PK, true, false>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-              default: break;
-            }
-            continue;
-          }
-          }
-          switch (rc.m) {
-            case 1: t_orbit<R, CS, 1, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-            case 2: t_orbit<R, CS, 2, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-            case 3: t_orbit<R, CS, 3, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-            case 4: t_orbit<R, CS, 4, PK>(rc, base, st_stride, cbr, KV, kv0, kv1, acc, pd.keep); break;
-            default: break;
-          }
+          t_record<R, CS, PK>((pd.keep & 0x8421u) != 0, rc, base, st_stride, cbr, KV, kv0, kv1,
+                              acc, pd.keep);
         }
         const R v = warp_transpose_sum<R>(acc, lane);
         if (pd.keep & (1u << (lane >> 1))) atomicAdd(tsm + ip * 32 + lane, v);
