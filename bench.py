@@ -1110,7 +1110,8 @@ SECTIONS.update({"dc_phase": lambda a, c: run_dc_phase(a, c),
                  "trotter": lambda a, c: run_trotter(a, c),
                  "operator_action": lambda a, c: run_operator_action(a, c),
                  "sampling": lambda a, c: run_sampling(a, c),
-                 "host_copies": lambda a, c: run_host_copies(a, c)})
+                 "host_copies": lambda a, c: run_host_copies(a, c),
+                 "largest": lambda a, c: run_largest(a, c)})
 
 if __name__ == "__main__":
     main()

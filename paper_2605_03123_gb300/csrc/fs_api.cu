@@ -474,6 +474,7 @@ int fs_destroy(fs_ctx* ctx) {
     for (auto& kv : ctx->spaces) free_space(kv.second);
     for (auto& kv : ctx->scratch) cudaFree(kv.second.ptr);
     cudaFree(ctx->d_status);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->tune_stream) cudaStreamDestroy(ctx->tune_stream);
     delete ctx;
@@ -1093,6 +1094,31 @@ namespace fs {
 // With dL = Re sum (R^-1 dR)_pq T_pq, the Euclidean gradient is R conj(T);
 // the chain rule through R_m = U_m^dag U_{m-1} and K -> expm(K) is FP64 host
 // work.
+// The context's mapped pinned staging buffer, grown to at least `bytes`
+// (growing allocates and frees pinned memory, which synchronizes the
+// device; it happens on the first calls only).
+static double* host_stage(Ctx* ctx, size_t bytes) {
+  if (ctx->h_stage_bytes < bytes) {
+    if (ctx->h_stage) FS_CUDA(cudaFreeHost(ctx->h_stage));
+    ctx->h_stage = nullptr;
+    ctx->h_stage_dev = nullptr;
+    ctx->h_stage_bytes = 0;
+    const size_t cap = std::max<size_t>(bytes, 1 << 17);
+    void* h = nullptr;
+    FS_CUDA(cudaHostAlloc(&h, cap, cudaHostAllocMapped));
+    void* d = nullptr;
+    const cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(h);
+      FS_CUDA(e);
+    }
+    ctx->h_stage = (double*)h;
+    ctx->h_stage_dev = (double*)d;
+    ctx->h_stage_bytes = cap;
+  }
+  return ctx->h_stage;
+}
+
 static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int dtype,
                           double* dK, double* dJ_aa, double* dJ_ab, cudaStream_t st) {
   const int n = op->norb, R = op->n_reps;
@@ -1236,14 +1262,18 @@ static void lucj_vjp_impl(Ctx* ctx, const fs_lucj* op, void* vec, void* cot, int
     launch_transpose(tpsi, vec, sb->dim, sa->dim, dtype, st);
     launch_transpose(tg, cot, sb->dim, sa->dim, dtype, st);
   }
-  std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn), dJT;
-  FS_CUDA(cudaMemcpyAsync(Th.data(), Tacc, Th.size() * 8, cudaMemcpyDeviceToHost, st));
-  FS_CUDA(cudaMemcpyAsync(dJh.data(), dJd, dJh.size() * 8, cudaMemcpyDeviceToHost, st));
-  if (alpha_t) {
-    dJT.resize(R * nn);
-    FS_CUDA(cudaMemcpyAsync(dJT.data(), dJabT_d, dJT.size() * 8, cudaMemcpyDeviceToHost, st));
+  std::vector<double> Th((R + 1) * nn * 2), dJh(2 * R * nn), dJT(alpha_t ? R * nn : 0);
+  {
+    // one small kernel writes the three results into the mapped host buffer
+    const size_t ntot = Th.size() + dJh.size() + dJT.size();
+    double* hs = host_stage(ctx, ntot * sizeof(double));
+    launch_gather_f64(Tacc, (int64_t)Th.size(), dJd, (int64_t)dJh.size(),
+                      alpha_t ? dJabT_d : nullptr, (int64_t)dJT.size(), ctx->h_stage_dev, st);
+    FS_CUDA(cudaStreamSynchronize(st));
+    std::copy(hs, hs + Th.size(), Th.begin());
+    std::copy(hs + Th.size(), hs + Th.size() + dJh.size(), dJh.begin());
+    std::copy(hs + Th.size() + dJh.size(), hs + ntot, dJT.begin());
   }
-  FS_CUDA(cudaStreamSynchronize(st));
   if (alpha_t)
     for (int k = 0; k < R; ++k)
       for (int p = 0; p < n; ++p)

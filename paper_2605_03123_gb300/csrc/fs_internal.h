@@ -212,6 +212,12 @@ struct Ctx {
   std::map<std::pair<int, int>, Space*> spaces;
   std::map<std::string, Scratch> scratch;
   int* d_status = nullptr;  // device status word
+  // small results the host needs right away (transition sums, coupling
+  // gradients) land in a mapped pinned buffer, written by a kernel: a copy
+  // through a copy engine would wait behind the caller's own large copies
+  double* h_stage = nullptr;      // host address
+  double* h_stage_dev = nullptr;  // its device address
+  size_t h_stage_bytes = 0;
   // private non-blocking stream on which batched launches are captured into
   // a graph (a capture cannot run on the legacy default stream); the graph
   // itself is launched on the caller's stream
@@ -502,6 +508,10 @@ void sample_state(Ctx* ctx, const void* vec, int dtype, int64_t n, const double*
 void sample_slater(Ctx* ctx, const std::vector<zd>& Phi, int N, int n, const double* u,
                    int64_t shots, uint64_t* out, cudaStream_t st);
 // out = in^T for a [rows][cols] complex state (tiled, HBM-bound).
+// out[0 .. na) = a, out[na .. na + nb) = b, out[na + nb .. na + nb + nc) = c
+// (b, c may be null with nb, nc = 0); out may be a mapped host address.
+void launch_gather_f64(const double* a, int64_t na, const double* b, int64_t nb,
+                       const double* c, int64_t nc, double* out, cudaStream_t st);
 void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
                       cudaStream_t st);
 void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, int dtype,

@@ -159,43 +159,66 @@ void launch_dc_grad(Ctx* ctx, const Space* sa, const Space* sb, const void* W, i
   FS_CUDA(cudaGetLastError());
 }
 
-// out[c][r] = in[r][c] for a rows x cols matrix of complex elements: square
-// tiles through shared memory, so reads and writes are both row-contiguous.
-template <typename T, int TILE>
+// out[c][r] = in[r][c] for a rows x cols matrix of complex elements: TR x TC
+// tiles (TR input rows, TC input columns) through shared memory, so reads
+// and writes are both row-contiguous.  256 threads read the tile as rows of
+// TC lanes and write it as rows of TR lanes; every thread keeps
+// TR * TC / 256 independent loads in flight.
+template <typename T, int TR, int TC>
 __global__ void __launch_bounds__(256)
     k_transpose(const T* __restrict__ in, T* __restrict__ out, int64_t rows, int64_t cols) {
-  // TILE x TILE tile; 256 threads as (256 / TILE) rows of TILE lanes, so a
-  // warp reads (and writes) 32 consecutive elements of one row, and every
-  // thread keeps TILE * TILE / 256 independent loads in flight
-  constexpr int RS = 256 / TILE;
-  __shared__ T tile[TILE][TILE + 1];
-  const int64_t c0 = (int64_t)blockIdx.x * TILE, r0 = (int64_t)blockIdx.y * TILE;
-  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
+  static_assert(256 % TC == 0 && 256 % TR == 0, "tile sides divide the block");
+  __shared__ T tile[TR][TC + 1];
+  const int64_t c0 = (int64_t)blockIdx.x * TC, r0 = (int64_t)blockIdx.y * TR;
+  {
+    const int tx = threadIdx.x % TC, ty = threadIdx.x / TC;
 #pragma unroll
-  for (int k = ty; k < TILE; k += RS) {
-    const int64_t r = r0 + k, c = c0 + tx;
-    if (r < rows && c < cols) tile[k][tx] = in[r * cols + c];
+    for (int k = ty; k < TR; k += 256 / TC) {
+      const int64_t r = r0 + k, c = c0 + tx;
+      if (r < rows && c < cols) tile[k][tx] = in[r * cols + c];
+    }
   }
   __syncthreads();
+  {
+    const int tx = threadIdx.x % TR, ty = threadIdx.x / TR;
 #pragma unroll
-  for (int k = ty; k < TILE; k += RS) {
-    const int64_t c = c0 + k, r = r0 + tx;
-    if (c < cols && r < rows) out[c * rows + r] = tile[tx][k];
+    for (int k = ty; k < TC; k += 256 / TR) {
+      const int64_t c = c0 + k, r = r0 + tx;
+      if (c < cols && r < rows) out[c * rows + r] = tile[tx][k];
+    }
   }
+}
+
+__global__ void k_gather_f64(const double* __restrict__ a, int64_t na,
+                             const double* __restrict__ b, int64_t nb,
+                             const double* __restrict__ c, int64_t nc, double* out) {
+  const int64_t n = na + nb + nc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = i < na ? a[i] : i < na + nb ? b[i - na] : c[i - na - nb];
+}
+
+void launch_gather_f64(const double* a, int64_t na, const double* b, int64_t nb,
+                       const double* c, int64_t nc, double* out, cudaStream_t st) {
+  const int64_t n = na + nb + nc;
+  if (n <= 0) return;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  k_gather_f64<<<blocks, 256, 0, st>>>(a, na, b, nb, c, nc, out);
+  FS_CUDA(cudaGetLastError());
 }
 
 void launch_transpose(const void* in, void* out, int64_t rows, int64_t cols, int dtype,
                       cudaStream_t st) {
   ProfScope ps("transpose", st);
-  if (dtype == FS_C64) {  // 64 x 64 tiles (33 KB of shared memory)
-    FS_REQUIRE((rows + 63) / 64 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
-    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
-    k_transpose<float2, 64><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, rows, cols);
+  if (dtype == FS_C64) {  // 32 x 64 tiles (17 KB of shared memory)
+    FS_REQUIRE((rows + 31) / 32 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
+    dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 31) / 32));
+    k_transpose<float2, 32, 64><<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, rows, cols);
   } else {  // 32 x 32 tiles of 16-byte elements (17 KB)
     FS_REQUIRE((rows + 31) / 32 <= 65535, FS_ERR_UNSUPPORTED, "transpose: too many rows");
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-    k_transpose<double2, 32><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, rows,
-                                                   cols);
+    k_transpose<double2, 32, 32><<<grid, 256, 0, st>>>((const double2*)in, (double2*)out, rows,
+                                                       cols);
   }
   FS_CUDA(cudaGetLastError());
 }
