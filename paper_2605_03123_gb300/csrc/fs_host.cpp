@@ -269,6 +269,13 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
     for (int i = 1; i <= b; ++i) r = r * (uint64_t)(a - b + i) / (uint64_t)i;
     return r;
   };
+  // Bank-aware order where one CTA holds a whole vector (complex64, psi and
+  // g: 16 bytes per string, at most 208 KB); larger spaces run on clusters,
+  // whose lists are regrouped by owning CTA, and keep the combinatorial
+  // order, under which a warp's strings mostly live on one CTA of the
+  // cluster (the bank-aware order made the N = 18 reverse sweeps 19 %
+  // slower).
+  const bool bank = C(N, n) * 16 <= 208 * 1024;
   for (int a = 0; a < npos; ++a) {
     off[a] = (int)orbits.size();
     std::vector<int> out;
@@ -338,7 +345,10 @@ void window_tables_host(int N, int n, int W, std::vector<uint32_t>& orbits,
           if (__builtin_popcount(S) == m)
             A[(size_t)i * ns + k++] = RO + offs[(((size_t)a * (n + 1) + clo) << W) + S];
       }
-      for (int i : bank_order(no_m, ns, A)) {
+      std::vector<int> ord(no_m);
+      for (int i = 0; i < no_m; ++i) ord[i] = i;
+      if (bank) ord = bank_order(no_m, ns, A);
+      for (int i : ord) {
         orbits.push_back(cls[m][i]);
         okey.push_back(ckey[m][i]);
       }
@@ -533,7 +543,10 @@ void tpass_tables_host(int N, int n, std::vector<TPass>& passes,
       std::vector<int> A((size_t)nr * ns);
       for (int i = 0; i < nr; ++i)
         for (int k = 0; k < ns; ++k) A[(size_t)i * ns + k] = rcls[m][i].addr[k];
-      for (int i : bank_order(nr, ns, A)) {
+      std::vector<int> ord(nr);
+      for (int i = 0; i < nr; ++i) ord[i] = i;
+      if (C(N, n) * 16 <= 208 * 1024) ord = bank_order(nr, ns, A);  // as for the windows
+      for (int i : ord) {
         recs.push_back(rcls[m][i]);
         rkey.push_back(rck[m][i]);
       }
