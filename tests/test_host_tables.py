@@ -19,7 +19,8 @@ combinatorial-number-system order of the paper's addressing, §3.1):
   reduction folds into the amplitudes;
 - the bank-aware order keeps the modelled shared-memory wavefronts of the
   16-byte gathers (eight lanes per wavefront, cell index mod 8 per bank
-  group) near the ideal at N = 16.
+  group) near the ideal at N = 16, and spaces too large for one CTA keep the
+  combinatorial order.
 """
 
 import os
@@ -202,3 +203,31 @@ def test_bank_aware_order_at_n16(driver):
             if g:
                 groups.append(g)
     assert _wavefronts(groups) < 1.7  # combinatorial order: 3.15
+
+
+def test_cluster_sized_spaces_keep_the_combinatorial_order(driver):
+    """N=17 (8): a complex64 vector of psi and g (24310 strings x 16 bytes)
+    exceeds one CTA, so the sweeps run on clusters and the lists stay in the
+    combinatorial order: within each class the outside configurations
+    ascend."""
+    N, n, W = 17, 8, 6
+    win, passes = _tables(driver, N, n, W)
+    strings = oracle.strings(N, n)
+    last = {}
+    for a, m, _, _, addrs in win:
+        if m == 0:
+            continue
+        wmask = ((1 << W) - 1) << a
+        outside = int(strings[addrs[0]]) & ~wmask
+        key = (a, m)
+        assert last.get(key, -1) < outside
+        last[key] = outside
+    for q, _, recs in passes[:3]:
+        qmask = sum(1 << x for x in q)
+        prev = {}
+        for rc in recs:
+            if rc is None:
+                continue
+            outside = int(strings[rc[3][0]]) & ~qmask
+            assert prev.get(rc[0], -1) < outside
+            prev[rc[0]] = outside
