@@ -242,7 +242,12 @@ int fs_lucj_forward(fs_ctx *ctx, const fs_lucj *op, void *vec, int dtype,
  *   dK:   n_reps*2*N*N doubles, dL/dRe K + i dL/dIm K for every entry;
  *   dJ_aa, dJ_ab: n_reps*N*N doubles, dL/dJ_pq with entries independent.
  * Host outputs; synchronizes the stream.  Any of dK, dJ_aa, dJ_ab may be
- * NULL to skip it. */
+ * NULL to skip it.  The device-side sums behind the gradients reach the host
+ * through a small mapped pinned buffer of the context (at least 128 KB,
+ * written by a kernel rather than copied by a copy engine, so that the
+ * call does not wait behind the caller's own large host copies); the first
+ * call on a context allocates it (an allocation of pinned memory, which
+ * synchronizes the device), and fs_destroy frees it. */
 int fs_lucj_vjp(fs_ctx *ctx, const fs_lucj *op, void *vec, void *cot,
                 int dtype, double *dK, double *dJ_aa, double *dJ_ab,
                 void *stream);
